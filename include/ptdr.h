@@ -1,0 +1,214 @@
+/*
+ * ptdr.h -- C ABI of libptdr, a GB300 (sm_103a) library for the Pauli
+ * decomposition of Koska, Baboulin and Gazda, "A tree-approach Pauli
+ * decomposition algorithm with application to quantum computing"
+ * (arXiv 2403.11644, "PTDR").
+ *
+ * What is computed (Sec. II.A, "Decomposition in the Pauli operator basis"
+ * and "Straightforward decomposition method"): for a complex 2^n x 2^n
+ * matrix A, all 4^n coefficients
+ *
+ *     c_P = 2^-n tr(P A),   P = sigma_{n-1} (x) ... (x) sigma_0,
+ *
+ * so that A = sum_P c_P P.  Operators are labelled with the paper's
+ * PauliComposer notation (Sec. II.B): qubit l <-> bit l of a row/column
+ * index, and P <-> two n-bit masks (x, z) with x_l = d(sigma_l) (1 for X and
+ * Y, the diagonality function) and z_l = 1 for Y and Z.  P_{x,z} has one
+ * nonzero per row j, at column j XOR x (Sec. II.A, "First optimization of
+ * the trace computation").
+ *
+ * Layouts (all row-major, complex numbers interleaved re, im):
+ *   A  : A[r * 2^n + c]                                     (2^n x 2^n)
+ *   C  : C[x * 2^n + z] = c_{P(x,z)}                        (4^n values)
+ *   band storage (Sec. IV.A, diagonal/tridiagonal/band-diagonal matrices):
+ *        bands[(d + s) * 2^n + c] = A[c + d][c],  d in [-s, s];
+ *        slots whose row c + d falls outside the matrix are ignored.
+ *
+ * Conventions shared by every entry point:
+ *   - All data pointers are DEVICE pointers owned by the caller, except the
+ *     arguments explicitly named h_* (host).  The library never allocates
+ *     device memory on these paths; scratch space is the caller-provided
+ *     workspace, whose size is queried first.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy
+ *     default stream).  Argument errors are returned synchronously before
+ *     anything is enqueued.  Errors detected on the device (a bounded wait
+ *     that ran out, an index check in a checked build) are recorded in a
+ *     device status word read by ptdr_last_device_status().
+ *   - There is no CPU fallback: without a usable CUDA device every compute
+ *     call returns PTDR_ERR_NO_DEVICE.
+ *   - Inputs and outputs must not overlap.  Pointers must be aligned to
+ *     their element size (16 bytes for complex types is recommended; the
+ *     vectorised paths need it and fall back to narrower loads otherwise).
+ */
+#ifndef PTDR_H
+#define PTDR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PTDR_OK = 0,
+    PTDR_ERR_INVALID_ARG = 1, /* null pointer, bad n/s/count, bad enum value, overlap */
+    PTDR_ERR_UNSUPPORTED = 2, /* valid but unsupported dtype/precision combination */
+    PTDR_ERR_NO_DEVICE = 3,   /* no CUDA device or driver; nothing was run */
+    PTDR_ERR_CUDA = 4,        /* a CUDA runtime call failed (launch, copy, attribute) */
+    PTDR_ERR_WORKSPACE = 5,   /* workspace null or smaller than the queried size */
+    PTDR_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up */
+    PTDR_ERR_INTERNAL = 7     /* device-side consistency check failed */
+} ptdr_status;
+
+typedef enum {
+    PTDR_C64 = 0,  /* complex float  (re, im float32) */
+    PTDR_C128 = 1, /* complex double (re, im float64) */
+    PTDR_F32 = 2,  /* real float32 */
+    PTDR_F64 = 3   /* real float64 */
+} ptdr_dtype;
+
+typedef enum {
+    /* float64 arithmetic on the FP64 pipe (full-accuracy mode) */
+    PTDR_PREC_FP64 = 0,
+    /* float32 arithmetic on the CUDA cores */
+    PTDR_PREC_FP32 = 1,
+    /* Hadamard stages as dense +-1 tensor-core tiles on bf16 hi/mid/lo splits
+       of float32 data, accumulated in float32 (the +-1 matrix is exact in bf16) */
+    PTDR_PREC_SPLIT_BF16_TC = 2,
+    /* same with fp16 hi/lo splits of power-of-two-scaled float32 data */
+    PTDR_PREC_SPLIT_FP16_TC = 3
+} ptdr_precision;
+
+typedef enum {
+    PTDR_OP_DECOMPOSE = 0,
+    PTDR_OP_COMPOSE = 1
+} ptdr_op;
+
+/*
+ * ptdr_decompose -- all 4^n coefficients of a dense matrix.
+ * Defines: c_P = 2^-n tr(P A) for every P in P_n (Sec. II.A; the paper's
+ * Algorithm 1 computes the same set by walking the Pauli tree, Sec. III.A).
+ *
+ *   A, a_type   device, 4^n elements of a_type in {C64, C128}, row-major.
+ *   C, c_type   device, 4^n elements of c_type in {C64, C128}; C[x*2^n + z].
+ *   n           1 <= n <= 15.
+ *   prec        FP64: any a_type/c_type.  FP32: any a_type/c_type (C128 input
+ *               is rounded to float32 on load).  SPLIT_*_TC: a_type = c_type
+ *               = C64.
+ *   workspace   device scratch of at least ptdr_workspace_size() bytes (may
+ *               be NULL when that size is 0).
+ * Returns PTDR_OK once the work is enqueued on `stream`.
+ */
+ptdr_status ptdr_decompose(const void* A, ptdr_dtype a_type, void* C, ptdr_dtype c_type, int n,
+                           ptdr_precision prec, void* workspace, size_t workspace_bytes,
+                           void* stream);
+
+/*
+ * ptdr_compose -- the inverse map: A = scale * sum_P c_P P.
+ * Defines: the expansion A = sum_P alpha_P P of Sec. II.A.  With scale = 1 it
+ * rebuilds A from ptdr_decompose's output; with scale = 2^-n it is the
+ * adjoint of ptdr_decompose (D(A)_P = 2^-n <P, A>), which is the backward
+ * pass of the decomposition for automatic differentiation.
+ *
+ *   C, c_type   device, 4^n coefficients, c_type in {C64, C128}.
+ *   A, a_type   device output, 4^n elements, a_type in {C64, C128}.
+ *   n, prec, workspace, stream as for ptdr_decompose (SPLIT_*_TC unsupported).
+ */
+ptdr_status ptdr_compose(const void* C, ptdr_dtype c_type, void* A, ptdr_dtype a_type, int n,
+                         double scale, ptdr_precision prec, void* workspace,
+                         size_t workspace_bytes, void* stream);
+
+/*
+ * ptdr_workspace_size -- device scratch bytes needed by ptdr_decompose or
+ * ptdr_compose for (n, a_type, c_type, prec).  Host only; no CUDA call.
+ */
+ptdr_status ptdr_workspace_size(ptdr_op op, int n, ptdr_dtype a_type, ptdr_dtype c_type,
+                                ptdr_precision prec, size_t* bytes);
+
+/*
+ * ptdr_structured_masks -- the X/Z-flip masks x that a band-diagonal matrix
+ * of half-width s can populate (s = 0: diagonal, s = 1: tridiagonal).
+ * Defines: Sec. IV.A.1 (diagonal: only I/Z terms, i.e. x = 0), Thm 3
+ * (tridiagonal: at most (n+1) 2^n terms) and Thm 4 (band-diagonal: at most
+ * (s n - c(s)) 2^n terms).  A mask x != 0 with highest set bit h is reachable
+ * iff 2^h - (x mod 2^h) <= s (the smallest |row - column| over the entries of
+ * the XOR-diagonal x).  Host only; no CUDA call.
+ *
+ *   n          1 <= n <= 40.   s >= 0.
+ *   h_masks    host output, ascending; may be NULL to query the count.
+ *   count      in: capacity of h_masks (ignored when h_masks is NULL);
+ *              out: number of masks.  Returns PTDR_ERR_INVALID_ARG if the
+ *              capacity is too small (count then holds the number needed).
+ */
+ptdr_status ptdr_structured_masks(int n, int s, uint64_t* h_masks, size_t* count);
+
+/*
+ * ptdr_decompose_structured -- the coefficients of a band-diagonal matrix on
+ * the given masks only (the paper prunes the X/Y subtrees, Sec. IV.A; here
+ * only the listed XOR-diagonals are gathered and transformed).
+ *
+ *   bands, b_type  device band storage (see layout above), (2s+1) * 2^n
+ *                  elements of b_type in {F32, F64, C64, C128}.
+ *   n, s           1 <= n <= 30, 0 <= s < 2^n.
+ *   h_masks        HOST array of n_masks masks (each < 2^n), e.g. from
+ *                  ptdr_structured_masks(); the launches are planned from it,
+ *                  so a mask list costs no device-side table.
+ *   C, c_type      device output, n_masks * 2^n elements; row i holds mask
+ *                  h_masks[i]: C[i * 2^n + z].  c_type complex, or real
+ *                  (F32/F64) for a real symmetric band input, whose
+ *                  coefficients are real (Thm 2): the real part is stored.
+ *   prec           FP64 or FP32.
+ *   workspace      at least ptdr_structured_workspace_size() bytes.
+ */
+ptdr_status ptdr_decompose_structured(const void* bands, ptdr_dtype b_type, int n, int s,
+                                      const uint64_t* h_masks, size_t n_masks, void* C,
+                                      ptdr_dtype c_type, ptdr_precision prec, void* workspace,
+                                      size_t workspace_bytes, void* stream);
+
+/* Workspace bytes for ptdr_decompose_structured.  Host only. */
+ptdr_status ptdr_structured_workspace_size(int n, int s, const uint64_t* h_masks, size_t n_masks,
+                                           ptdr_dtype b_type, ptdr_dtype c_type,
+                                           ptdr_precision prec, size_t* bytes);
+
+/*
+ * ptdr_decompose_batched -- decomposes `count` independent matrices of
+ * possibly different sizes in one persistent launch (the paper's forest of
+ * independent subtrees, Sec. V.B, taken across matrices).
+ *
+ *   d_A      device array of `count` device pointers to the inputs.
+ *   d_C      device array of `count` device pointers to the outputs.
+ *   d_n      device array of `count` sizes n_i.
+ *   h_n      the same sizes on the host (sizes the grid and workspace).
+ *   count    >= 1.  1 <= n_i <= 13.
+ *   a_type, c_type, prec as for ptdr_decompose (FP32 or FP64).
+ *   workspace at least ptdr_batched_workspace_size() bytes.
+ * The launch sequence is fixed for a given h_n, so it can be captured in a
+ * CUDA graph and replayed with new data behind the same pointers.
+ */
+ptdr_status ptdr_decompose_batched(const void* const* d_A, void* const* d_C, const int* d_n,
+                                   const int* h_n, int count, ptdr_dtype a_type,
+                                   ptdr_dtype c_type, ptdr_precision prec, void* workspace,
+                                   size_t workspace_bytes, void* stream);
+
+/* Workspace bytes for ptdr_decompose_batched.  Host only. */
+ptdr_status ptdr_batched_workspace_size(const int* h_n, int count, ptdr_dtype a_type,
+                                        ptdr_dtype c_type, ptdr_precision prec, size_t* bytes);
+
+/*
+ * ptdr_last_device_status -- synchronises `stream`, returns the status word
+ * the kernels wrote since the previous call (PTDR_OK if none) and clears it.
+ */
+ptdr_status ptdr_last_device_status(void* stream);
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char* ptdr_status_string(ptdr_status status);
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+int ptdr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PTDR_H */

@@ -1,0 +1,174 @@
+// Band-diagonal matrices (Sec. IV.A of the paper): only the masks a band of
+// half-width s can reach are transformed, and within a mask only the entries
+// inside the band.
+//
+// For a mask x, entry k of the XOR-diagonal d_x[k] = A[k^x][k] lies at
+// row - column = x - 2 (k & x), so it is inside the band only for the few
+// t = k & x in T_x = { t subset of x : |x - 2t| <= s }.  Writing k = t | u'
+// with u' a subset of the free bits F = ~x,
+//     WHT(d_x)[z] = sum_{t in T_x} (-1)^{|z & t|} V_t[compress_F(z)],
+//     V_t = WHT over the |F| free bits of g_t[u] = band_{x-2t}[t | expand_F(u)],
+// so each mask costs |T_x| transforms of length 2^{n-|x|} plus one
+// expansion pass, instead of a full length-2^n transform (the pruned X/Y
+// subtrees of Sec. IV.A; for the tridiagonal masks 2^m - 1, |T_x| = 2).
+#include "tile_ops.cuh"
+#include "structured.h"
+
+namespace ptdr {
+
+// Spreads the low bits of u over the free (zero) bits of x: the zeros of x
+// below bit h1 = msb(x) + 1 take the low zc bits of u in order, every bit at
+// or above h1 is free and takes the rest of u as a plain shift.
+__device__ __forceinline__ uint64_t expand_free(uint64_t u, uint64_t x, int h1, int zc)
+{
+    uint64_t out = (u >> zc) << h1;
+    uint64_t zeros = ~x & ((1ull << h1) - 1);
+    uint64_t lo = u;
+    while (zeros) {
+        const int b = __ffsll((long long)zeros) - 1;
+        zeros &= zeros - 1;
+        out |= (lo & 1ull) << b;
+        lo >>= 1;
+    }
+    return out;
+}
+
+// Inverse of expand_free on the free bits: the bits of z at the zeros of x
+// below h1, packed, then the bits of z at and above h1.
+__device__ __forceinline__ uint64_t compress_free(uint64_t z, uint64_t x, int h1, int zc)
+{
+    uint64_t out = (z >> h1) << zc;
+    uint64_t zeros = ~x & ((1ull << h1) - 1);
+    int j = 0;
+    while (zeros) {
+        const int b = __ffsll((long long)zeros) - 1;
+        zeros &= zeros - 1;
+        out |= ((z >> b) & 1ull) << j;
+        ++j;
+    }
+    return out;
+}
+
+// First pass: one CTA per (pair j, segment of 2^log_l values of u).
+template <typename T, typename BandT>
+__global__ void __launch_bounds__(512) k_band_first(BandMaskLaunch p, unsigned int* st)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    using T2 = cplx_t<T>;
+    T2* s = reinterpret_cast<T2*>(smem_raw);
+    const Smem sm = make_smem(p.log_l);
+    const int segs_log = p.f - p.log_l;
+    const int j = blockIdx.x >> segs_log;
+    const uint64_t seg = (uint64_t)blockIdx.x & ((1ull << segs_log) - 1);
+    const uint64_t N = 1ull << p.n;
+    const uint64_t t = p.t[j];
+    const int64_t d = p.d[j];
+    const BandT* band = (const BandT*)p.bands + (uint64_t)(d + p.s) * N;
+    const int L = 1 << p.log_l;
+    const uint64_t bands_elems = (uint64_t)(2 * p.s + 1) * N;
+    for (int e = threadIdx.x; e < L; e += blockDim.x) {
+        const uint64_t u = (seg << p.log_l) + (uint64_t)e;
+        const uint64_t k = t | expand_free(u, p.x, p.h1, p.zc);
+        const uint64_t gi = (uint64_t)(d + p.s) * N + k;
+        T2 v = mk<T>(0, 0);
+        if (in_bounds(st, gi, bands_elems)) v = io<BandT>::template ld<T>(band + k);
+        s[sm.idx(e)] = v;
+    }
+    __syncthreads();
+    wht_bits(s, sm, p.log_l, 0, p.log_l);
+    T2* out = (T2*)p.ws;
+    const uint64_t row = (uint64_t)j << p.f;
+    for (int e = threadIdx.x; e < L; e += blockDim.x) {
+        const uint64_t gi = row + (seg << p.log_l) + (uint64_t)e;
+        if (in_bounds(st, gi, p.ws_elems)) out[gi] = s[sm.idx(e)];
+    }
+}
+
+// Expansion: C[row][z] = scale (-i)^{|x&z|} sum_j (-1)^{|z & t_j|} V_j[compress_F(z)].
+template <typename T, typename OutT>
+__global__ void __launch_bounds__(256) k_band_expand(BandMaskLaunch p, unsigned int* st)
+{
+    using T2 = cplx_t<T>;
+    const uint64_t N = 1ull << p.n;
+    const T2* V = (const T2*)p.ws;
+    const T scale = (T)p.scale;
+    for (uint64_t z = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; z < N;
+         z += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t v = compress_free(z, p.x, p.h1, p.zc);
+        T2 acc = mk<T>(0, 0);
+        for (int j = 0; j < p.npairs; ++j) {
+            const uint64_t gi = ((uint64_t)j << p.f) + v;
+            T2 w = mk<T>(0, 0);
+            if (in_bounds(st, gi, p.ws_elems)) w = V[gi];
+            acc = (__popcll(z & p.t[j]) & 1) ? csub(acc, w) : cadd(acc, w);
+        }
+        const T2 c = phase_neg_i(acc, __popcll(p.x & z), scale);
+        const uint64_t gi = p.out_row * N + z;
+        if (in_bounds(st, gi, p.out_elems)) io<OutT>::st((OutT*)p.out + gi, c);
+    }
+}
+
+template <typename K>
+static cudaError_t set_smem(K kernel, size_t bytes)
+{
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <typename T, typename BandT>
+static cudaError_t run_first(const BandMaskLaunch& p, unsigned int* st, cudaStream_t s)
+{
+    auto kern = k_band_first<T, BandT>;
+    const size_t bytes = smem_elems(1, p.log_l) * sizeof(cplx_t<T>);
+    cudaError_t e = set_smem(kern, bytes);
+    if (e != cudaSuccess) return e;
+    const unsigned blocks = (unsigned)p.npairs << (p.f - p.log_l);
+    kern<<<blocks, p.threads, bytes, s>>>(p, st);
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t first_by_band(const BandMaskLaunch& p, unsigned int* st, cudaStream_t s)
+{
+    switch (p.b_t) {
+    case PTDR_F32: return run_first<T, float>(p, st, s);
+    case PTDR_F64: return run_first<T, double>(p, st, s);
+    case PTDR_C64: return run_first<T, float2>(p, st, s);
+    case PTDR_C128: return run_first<T, double2>(p, st, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_band_first(const BandMaskLaunch& p, unsigned int* st, cudaStream_t s)
+{
+    return p.calc == Calc::F32 ? first_by_band<float>(p, st, s) : first_by_band<double>(p, st, s);
+}
+
+template <typename T, typename OutT>
+static cudaError_t run_expand(const BandMaskLaunch& p, unsigned int* st, cudaStream_t s)
+{
+    const uint64_t N = 1ull << p.n;
+    const uint64_t want = (N + 255) / 256;
+    const unsigned blocks = (unsigned)(want < 152ull * 16 ? want : 152ull * 16);
+    k_band_expand<T, OutT><<<blocks, 256, 0, s>>>(p, st);
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t expand_by_out(const BandMaskLaunch& p, unsigned int* st, cudaStream_t s)
+{
+    switch (p.c_t) {
+    case PTDR_F32: return run_expand<T, float>(p, st, s);
+    case PTDR_F64: return run_expand<T, double>(p, st, s);
+    case PTDR_C64: return run_expand<T, float2>(p, st, s);
+    case PTDR_C128: return run_expand<T, double2>(p, st, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_band_expand(const BandMaskLaunch& p, unsigned int* st, cudaStream_t s)
+{
+    return p.calc == Calc::F32 ? expand_by_out<float>(p, st, s) : expand_by_out<double>(p, st, s);
+}
+
+} // namespace ptdr

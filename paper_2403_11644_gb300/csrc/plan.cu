@@ -1,0 +1,166 @@
+// Host-side planning and execution of the dense decompose/compose launches.
+#include <algorithm>
+
+#include "plan.h"
+
+namespace ptdr {
+
+static int ilog2(size_t v)
+{
+    int l = 0;
+    while (((size_t)1 << (l + 1)) <= v) ++l;
+    return l;
+}
+
+std::vector<StridedPass> strided_schedule(int b0, int n, size_t elem_bytes)
+{
+    // Each strided tile is 2^nb rows (the bits transformed) x 2^log_w
+    // consecutive elements (>= 32 bytes so that every row piece is a whole
+    // sector); as many bits per pass as the tile budget allows.
+    std::vector<StridedPass> out;
+    const int tile_log = ilog2(kTileBytes / elem_bytes);
+    const int min_w = std::max(0, ilog2(32 / elem_bytes));
+    int b = b0;
+    while (b < n) {
+        int nb = std::min(n - b, tile_log - min_w);
+        int log_w = std::min(tile_log - nb, b); // columns come from the bits below b
+        out.push_back({b, b + nb, log_w});
+        b += nb;
+    }
+    return out;
+}
+
+ptdr_status make_dense_plan(bool compose, int n, ptdr_dtype in_t, ptdr_dtype out_t,
+                            ptdr_precision prec, DensePlan* plan)
+{
+    if (prec == PTDR_PREC_SPLIT_BF16_TC || prec == PTDR_PREC_SPLIT_FP16_TC)
+        return PTDR_ERR_UNSUPPORTED; // tensor-core path not built yet
+    DensePlan p;
+    p.compose = compose;
+    p.n = n;
+    p.in_t = in_t;
+    p.out_t = out_t;
+    p.prec = prec;
+    p.calc = prec == PTDR_PREC_FP64 ? Calc::F64 : Calc::F32;
+    const size_t S = p.calc == Calc::F64 ? 16 : 8;
+    const size_t N = (size_t)1 << n;
+    const size_t row_bytes = N * S;
+    if (row_bytes <= kRowTileBytes) {
+        p.single = true;
+        p.log_l = n;
+        int lr = 0;
+        while (lr < 4 && lr < n && (row_bytes << (lr + 1)) <= std::max(row_bytes, kTileBytes)) ++lr;
+        p.log_r = lr;
+        const size_t tile = row_bytes << lr;
+        p.threads = tile >= 32 * 1024 ? 512 : 256;
+    } else {
+        p.single = false;
+        p.log_r = 0;
+        p.log_l = ilog2(kTileBytes / S);
+        p.threads = 512;
+        p.passes = strided_schedule(p.log_l, n, S);
+        // Decompose can keep the intermediate in C when C has the compute
+        // type; compose scatters into A, so its intermediate never aliases A.
+        const bool same = (p.calc == Calc::F32 && out_t == PTDR_C64) ||
+                          (p.calc == Calc::F64 && out_t == PTDR_C128);
+        p.buf_is_out = !compose && same;
+        if (p.buf_is_out) {
+            p.chunk = N;
+            p.ws_bytes = 0;
+        } else {
+            p.chunk = std::max<size_t>(1, std::min<size_t>(N, kChunkBytes / row_bytes));
+            p.ws_bytes = p.chunk * row_bytes;
+        }
+    }
+    *plan = p;
+    return PTDR_OK;
+}
+
+ptdr_status execute_dense(const DensePlan& p, const void* in, void* out, void* ws, double scale,
+                          unsigned int* st, cudaStream_t s)
+{
+    const uint64_t N = 1ull << p.n;
+    cudaError_t e = cudaSuccess;
+    if (p.single) {
+        TileLaunch t{};
+        t.src = in;
+        t.dst = out;
+        t.src_t = p.in_t;
+        t.dst_t = p.out_t;
+        t.calc = p.calc;
+        t.load = p.compose ? Load::RowPhaseC : Load::GatherA;
+        t.store = p.compose ? Store::ScatterA : Store::RowPhaseOut;
+        t.n = p.n;
+        t.log_r = p.log_r;
+        t.log_l = p.log_l;
+        t.x_begin = 0;
+        t.x_count = N;
+        t.dst_row0 = 0;
+        t.src_row0 = 0;
+        t.src_elems = N * N;
+        t.dst_elems = N * N;
+        t.scale = scale;
+        t.threads = p.threads;
+        e = launch_tile(t, st, s);
+        return e == cudaSuccess ? PTDR_OK : PTDR_ERR_CUDA;
+    }
+    for (uint64_t x0 = 0; x0 < N && e == cudaSuccess; x0 += p.chunk) {
+        void* buf = p.buf_is_out ? out : ws;
+        const uint64_t buf_row0 = p.buf_is_out ? 0 : x0;
+        const uint64_t buf_elems = p.buf_is_out ? N * N : p.chunk * N;
+        TileLaunch t{};
+        t.src = in;
+        t.dst = buf;
+        t.src_t = p.in_t;
+        t.dst_t = p.out_t; // unused for RowBuf
+        t.calc = p.calc;
+        t.load = p.compose ? Load::RowPhaseC : Load::GatherA;
+        t.store = Store::RowBuf;
+        t.n = p.n;
+        t.log_r = 0;
+        t.log_l = p.log_l;
+        t.x_begin = x0;
+        t.x_count = p.chunk;
+        t.dst_row0 = buf_row0;
+        t.src_row0 = 0;
+        t.src_elems = N * N;
+        t.dst_elems = buf_elems;
+        // compose applies its scale with the phase on load; decompose at the end
+        t.scale = p.compose ? scale : 1.0;
+        t.threads = p.threads;
+        e = launch_tile(t, st, s);
+        for (size_t i = 0; i < p.passes.size() && e == cudaSuccess; ++i) {
+            const bool last = i + 1 == p.passes.size();
+            StridedLaunch q{};
+            q.src = buf;
+            q.src_t = p.out_t;
+            q.calc = p.calc;
+            q.n = p.n;
+            q.b0 = p.passes[i].b0;
+            q.b1 = p.passes[i].b1;
+            q.log_w = p.passes[i].log_w;
+            q.x_begin = x0;
+            q.x_count = p.chunk;
+            q.src_row0 = buf_row0;
+            q.src_elems = buf_elems;
+            q.dst_elems = last ? N * N : buf_elems;
+            q.threads = 512;
+            if (!last) {
+                q.dst = buf;
+                q.store = Store::RowBuf;
+                q.dst_row0 = buf_row0;
+                q.scale = 1.0;
+            } else {
+                q.dst = out;
+                q.dst_t = p.out_t;
+                q.store = p.compose ? Store::ScatterA : Store::RowPhaseOut;
+                q.dst_row0 = 0;
+                q.scale = p.compose ? 1.0 : scale;
+            }
+            e = launch_strided(q, st, s);
+        }
+    }
+    return e == cudaSuccess ? PTDR_OK : PTDR_ERR_CUDA;
+}
+
+} // namespace ptdr

@@ -1,0 +1,58 @@
+// Launch planning for the dense decompose/compose paths (host side).
+#pragma once
+
+#include <vector>
+
+#include "ptdr_internal.h"
+
+namespace ptdr {
+
+constexpr int kMaxDenseN = 15;
+
+// Shared-memory budget of one tile of the generic kernels (bytes, unpadded).
+constexpr size_t kTileBytes = 64 * 1024;
+// A whole row in one tile is allowed up to this size (one CTA per SM).
+constexpr size_t kRowTileBytes = 128 * 1024;
+// Workspace cap for the intermediate of chunked multi-pass launches.
+constexpr size_t kChunkBytes = 256ull << 20;
+
+struct StridedPass {
+    int b0, b1, log_w;
+};
+
+enum class DenseKernel {
+    Tiles,      // generic tile kernels (any n, FP32/FP64)
+};
+
+struct DensePlan {
+    bool compose = false;
+    int n = 0;
+    ptdr_dtype in_t = PTDR_C64, out_t = PTDR_C64;
+    ptdr_precision prec = PTDR_PREC_FP32;
+    Calc calc = Calc::F32;
+    DenseKernel kernel = DenseKernel::Tiles;
+    bool single = true;      // one tile pass covers a whole row
+    int log_r = 0, log_l = 0; // first pass tile
+    int threads = 256;
+    std::vector<StridedPass> passes;
+    bool buf_is_out = false; // intermediate lives in the output array
+    uint64_t chunk = 0;      // masks per launch chunk (multi-pass)
+    size_t ws_bytes = 0;
+};
+
+ptdr_status make_dense_plan(bool compose, int n, ptdr_dtype in_t, ptdr_dtype out_t,
+                            ptdr_precision prec, DensePlan* plan);
+ptdr_status execute_dense(const DensePlan& plan, const void* in, void* out, void* ws,
+                          double scale, unsigned int* status, cudaStream_t s);
+
+// Splits bits [b0, n) into strided passes whose tiles fit kTileBytes.
+std::vector<StridedPass> strided_schedule(int b0, int n, size_t elem_bytes);
+
+// shared helpers (ptdr_api.cu)
+ptdr_status device_ready(int* dev);
+ptdr_status status_word(int dev, unsigned int** out);
+ptdr_status check_device_ptr(const void* p);
+bool overlaps(const void* a, size_t na, const void* b, size_t nb);
+bool fault_injected(const char* what);
+
+} // namespace ptdr

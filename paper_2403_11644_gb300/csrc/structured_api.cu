@@ -1,0 +1,223 @@
+// Band-diagonal (structured) entry points: mask enumeration on the host.
+#include "plan.h"
+
+using namespace ptdr;
+
+extern "C" {
+
+// A mask x != 0 with highest set bit h reaches the band iff the smallest
+// |row - column| over its XOR-diagonal, 2^h - (x mod 2^h), is at most s
+// (Sec. IV.A: diagonal, Thm 3 tridiagonal, Thm 4 band-diagonal).
+ptdr_status ptdr_structured_masks(int n, int s, uint64_t* h_masks, size_t* count)
+{
+    if (!count || n < 1 || n > 40 || s < 0) return PTDR_ERR_INVALID_ARG;
+    const uint64_t N = 1ull << n;
+    const size_t cap = h_masks ? *count : 0;
+    size_t cnt = 0;
+    auto emit = [&](uint64_t x) {
+        if (h_masks && cnt < cap) h_masks[cnt] = x;
+        ++cnt;
+    };
+    emit(0);
+    for (int h = 0; h < n; ++h) {
+        const uint64_t top = 1ull << h;
+        // x = top + rest with rest < top; reachable iff top - rest <= s,
+        // i.e. rest >= top - s (all rest when s >= top).
+        const uint64_t lo = (uint64_t)s >= top ? 0 : top - (uint64_t)s;
+        for (uint64_t rest = lo; rest < top; ++rest) {
+            if (top + rest >= N) break;
+            emit(top + rest);
+        }
+    }
+    *count = cnt;
+    if (h_masks && cnt > cap) return PTDR_ERR_INVALID_ARG;
+    return PTDR_OK;
+}
+
+} // extern "C"
+
+// ---------------------------------------------------------------- planning
+
+#include <cmath>
+#include <vector>
+
+#include "structured.h"
+
+namespace {
+
+struct MaskPlan {
+    uint64_t x;
+    int h1, zc, f, npairs;
+    uint64_t t[kMaxBandPairs];
+    int64_t d[kMaxBandPairs];
+};
+
+int msb1(uint64_t x)
+{
+    int h = 0;
+    while (x >> h) ++h;
+    return h; // msb + 1, 0 for x = 0
+}
+
+// T_x = { t subset of x : |x - 2t| <= s }: t lies in [(x-s)/2, (x+s)/2].
+MaskPlan plan_mask(int n, int s, uint64_t x)
+{
+    MaskPlan m{};
+    m.x = x;
+    m.h1 = msb1(x);
+    m.zc = m.h1 - __builtin_popcountll(x);
+    m.f = n - __builtin_popcountll(x);
+    const int64_t lo = ((int64_t)x - s + 1) / 2 > 0 ? ((int64_t)x - s + 1) / 2 : 0;
+    const int64_t hi = ((int64_t)x + s) / 2;
+    for (int64_t t = lo; t <= hi; ++t) {
+        if (((uint64_t)t & ~x) != 0) continue;
+        const int64_t d = (int64_t)x - 2 * t;
+        if (d < -s || d > s) continue;
+        m.t[m.npairs] = (uint64_t)t;
+        m.d[m.npairs] = d;
+        ++m.npairs;
+    }
+    return m;
+}
+
+size_t calc_bytes(ptdr_precision p) { return p == PTDR_PREC_FP64 ? 16 : 8; }
+
+ptdr_status validate_structured(const void* bands, ptdr_dtype b_t, int n, int s,
+                                const uint64_t* h_masks, size_t n_masks, ptdr_dtype c_t,
+                                ptdr_precision prec)
+{
+    if (!bands || !h_masks || n_masks == 0) return PTDR_ERR_INVALID_ARG;
+    if (n < 1 || n > 30 || s < 0) return PTDR_ERR_INVALID_ARG;
+    const uint64_t N = 1ull << n;
+    if ((uint64_t)s >= N) return PTDR_ERR_INVALID_ARG;
+    if (s >= kMaxBandPairs) return PTDR_ERR_UNSUPPORTED;
+    if ((int)b_t < PTDR_C64 || (int)b_t > PTDR_F64 || (int)c_t < PTDR_C64 || (int)c_t > PTDR_F64)
+        return PTDR_ERR_INVALID_ARG;
+    if ((int)prec < PTDR_PREC_FP64 || (int)prec > PTDR_PREC_SPLIT_FP16_TC) return PTDR_ERR_INVALID_ARG;
+    if (prec != PTDR_PREC_FP64 && prec != PTDR_PREC_FP32) return PTDR_ERR_UNSUPPORTED;
+    if (!dtype_complex(c_t) && dtype_complex(b_t)) return PTDR_ERR_UNSUPPORTED;
+    for (size_t i = 0; i < n_masks; ++i)
+        if (h_masks[i] >= N) return PTDR_ERR_INVALID_ARG;
+    return PTDR_OK;
+}
+
+size_t structured_ws(int n, int s, const uint64_t* h_masks, size_t n_masks, ptdr_precision prec)
+{
+    size_t mx = 0;
+    for (size_t i = 0; i < n_masks; ++i) {
+        MaskPlan m = plan_mask(n, s, h_masks[i]);
+        mx = std::max(mx, ((size_t)m.npairs << m.f) * calc_bytes(prec));
+    }
+    return mx;
+}
+
+} // namespace
+
+extern "C" {
+
+ptdr_status ptdr_structured_workspace_size(int n, int s, const uint64_t* h_masks, size_t n_masks,
+                                           ptdr_dtype b_type, ptdr_dtype c_type,
+                                           ptdr_precision prec, size_t* bytes)
+{
+    if (!bytes) return PTDR_ERR_INVALID_ARG;
+    // bands pointer not needed for sizing: pass a dummy non-null value
+    ptdr_status v = validate_structured((const void*)1, b_type, n, s, h_masks, n_masks, c_type, prec);
+    if (v != PTDR_OK) return v;
+    *bytes = structured_ws(n, s, h_masks, n_masks, prec);
+    return PTDR_OK;
+}
+
+ptdr_status ptdr_decompose_structured(const void* bands, ptdr_dtype b_type, int n, int s,
+                                      const uint64_t* h_masks, size_t n_masks, void* C,
+                                      ptdr_dtype c_type, ptdr_precision prec, void* workspace,
+                                      size_t workspace_bytes, void* stream)
+{
+    if (!C) return PTDR_ERR_INVALID_ARG;
+    ptdr_status v = validate_structured(bands, b_type, n, s, h_masks, n_masks, c_type, prec);
+    if (v != PTDR_OK) return v;
+    const uint64_t N = 1ull << n;
+    const size_t band_bytes = (size_t)(2 * s + 1) * N * dtype_bytes(b_type);
+    const size_t out_bytes = n_masks * N * dtype_bytes(c_type);
+    if ((uintptr_t)bands % dtype_bytes(b_type) || (uintptr_t)C % dtype_bytes(c_type))
+        return PTDR_ERR_INVALID_ARG;
+    if (overlaps(bands, band_bytes, C, out_bytes)) return PTDR_ERR_INVALID_ARG;
+    const size_t need = structured_ws(n, s, h_masks, n_masks, prec);
+    if (need > 0 && (!workspace || workspace_bytes < need)) return PTDR_ERR_WORKSPACE;
+    if (need > 0 && overlaps(workspace, need, C, out_bytes)) return PTDR_ERR_INVALID_ARG;
+    if (fault_injected("plan")) return PTDR_ERR_INTERNAL;
+    int dev = 0;
+    v = device_ready(&dev);
+    if (v != PTDR_OK) return v;
+    if (check_device_ptr(bands) != PTDR_OK || check_device_ptr(C) != PTDR_OK ||
+        (need > 0 && check_device_ptr(workspace) != PTDR_OK))
+        return PTDR_ERR_INVALID_ARG;
+    unsigned int* st = nullptr;
+    v = status_word(dev, &st);
+    if (v != PTDR_OK) return v;
+    if (fault_injected("launch")) return PTDR_ERR_CUDA;
+
+    cudaStream_t cs = (cudaStream_t)stream;
+    const Calc calc = prec == PTDR_PREC_FP64 ? Calc::F64 : Calc::F32;
+    const size_t S = calc_bytes(prec);
+    int single_log = 0, tile_log = 0;
+    while (((size_t)2 << single_log) * S <= kRowTileBytes) ++single_log;
+    while (((size_t)2 << tile_log) * S <= kTileBytes) ++tile_log;
+    cudaError_t e = cudaSuccess;
+    for (size_t i = 0; i < n_masks && e == cudaSuccess; ++i) {
+        MaskPlan m = plan_mask(n, s, h_masks[i]);
+        BandMaskLaunch p{};
+        p.bands = bands;
+        p.b_t = b_type;
+        p.c_t = c_type;
+        p.calc = calc;
+        p.n = n;
+        p.s = s;
+        p.x = m.x;
+        p.h1 = m.h1;
+        p.zc = m.zc;
+        p.f = m.f;
+        p.npairs = m.npairs;
+        for (int j = 0; j < m.npairs; ++j) {
+            p.t[j] = m.t[j];
+            p.d[j] = m.d[j];
+        }
+        p.ws = workspace;
+        p.ws_elems = (uint64_t)m.npairs << m.f;
+        p.out = C;
+        p.out_row = i;
+        p.out_elems = (uint64_t)n_masks * N;
+        p.scale = std::ldexp(1.0, -n);
+        const bool single = m.f <= single_log;
+        p.log_l = single ? m.f : tile_log;
+        p.threads = ((size_t)1 << p.log_l) * S >= 32 * 1024 ? 512 : 256;
+        // A mask the band cannot reach has no pairs: its row is written as zeros.
+        if (m.npairs > 0) e = launch_band_first(p, st, cs);
+        if (e == cudaSuccess && m.npairs > 0 && !single) {
+            std::vector<StridedPass> passes = strided_schedule(p.log_l, m.f, S);
+            for (size_t q = 0; q < passes.size() && e == cudaSuccess; ++q) {
+                StridedLaunch sl{};
+                sl.src = workspace;
+                sl.dst = workspace;
+                sl.calc = calc;
+                sl.store = Store::RowBuf;
+                sl.n = m.f;
+                sl.b0 = passes[q].b0;
+                sl.b1 = passes[q].b1;
+                sl.log_w = passes[q].log_w;
+                sl.x_begin = 0;
+                sl.x_count = (uint64_t)m.npairs;
+                sl.src_row0 = 0;
+                sl.dst_row0 = 0;
+                sl.src_elems = p.ws_elems;
+                sl.dst_elems = p.ws_elems;
+                sl.scale = 1.0;
+                sl.threads = 512;
+                e = launch_strided(sl, st, cs);
+            }
+        }
+        if (e == cudaSuccess) e = launch_band_expand(p, st, cs);
+    }
+    return e == cudaSuccess ? PTDR_OK : PTDR_ERR_CUDA;
+}
+
+} // extern "C"

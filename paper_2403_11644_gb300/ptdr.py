@@ -1,0 +1,222 @@
+"""PyTorch-facing API over libptdr's C ABI.
+
+Torch supplies device memory and the current stream; every step of the
+decomposition runs in libptdr's CUDA kernels.  Tensors must be CUDA tensors;
+there is no CPU path.
+
+Output layout: ``C[x, z] = c_{P(x,z)} = 2^-n tr(P A)`` with the paper's
+PauliComposer masks (Sec. II.B): x_l = 1 for X/Y on qubit l, z_l = 1 for Y/Z;
+qubit l is bit l of the row/column index (P = sigma_{n-1} (x) ... (x) sigma_0).
+"""
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import check
+
+PRECISIONS = {
+    "fp64": _lib.PREC_FP64,
+    "fp32": _lib.PREC_FP32,
+    "bf16x3": _lib.PREC_SPLIT_BF16_TC,
+    "fp16x2": _lib.PREC_SPLIT_FP16_TC,
+}
+_DT = {torch.complex64: _lib.C64, torch.complex128: _lib.C128, torch.float32: _lib.F32,
+       torch.float64: _lib.F64}
+
+
+def _dtype_code(t: torch.dtype) -> int:
+    if t not in _DT:
+        raise TypeError(f"unsupported dtype {t}")
+    return _DT[t]
+
+
+def _n_of(N: int) -> int:
+    if N < 2 or N & (N - 1):
+        raise ValueError("matrix size must be a power of two >= 2")
+    return N.bit_length() - 1
+
+
+def _stream(dev) -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+
+
+def _cuda(t: torch.Tensor, name: str) -> torch.Tensor:
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor (libptdr has no CPU path)")
+    return t.contiguous()
+
+
+def _workspace(nbytes: int, dev) -> torch.Tensor:
+    return torch.empty(max(nbytes, 1), dtype=torch.uint8, device=dev)
+
+
+def _prec(precision: str) -> int:
+    if precision not in PRECISIONS:
+        raise ValueError(f"precision must be one of {sorted(PRECISIONS)}")
+    return PRECISIONS[precision]
+
+
+def workspace_size(op: str, n: int, a_dtype, c_dtype, precision: str) -> int:
+    out = ctypes.c_size_t(0)
+    code = _lib.OP_DECOMPOSE if op == "decompose" else _lib.OP_COMPOSE
+    check(_lib.load().ptdr_workspace_size(code, n, _dtype_code(a_dtype), _dtype_code(c_dtype),
+                                          _prec(precision), ctypes.byref(out)), "ptdr_workspace_size")
+    return out.value
+
+
+def decompose(A: torch.Tensor, precision: str = "fp32", out_dtype=None, out=None,
+              workspace=None) -> torch.Tensor:
+    """All 4^n coefficients ``C[x, z]`` of a 2^n x 2^n complex CUDA matrix."""
+    A = _cuda(A, "A")
+    n = _n_of(A.shape[0])
+    if A.shape != (1 << n, 1 << n):
+        raise ValueError("A must be square")
+    if out_dtype is None:
+        out_dtype = torch.complex128 if precision == "fp64" else torch.complex64
+    C = out if out is not None else torch.empty((1 << n, 1 << n), dtype=out_dtype, device=A.device)
+    ws_bytes = workspace_size("decompose", n, A.dtype, C.dtype, precision)
+    ws = workspace if workspace is not None else (_workspace(ws_bytes, A.device) if ws_bytes else None)
+    check(_lib.load().ptdr_decompose(
+        ctypes.c_void_p(A.data_ptr()), _dtype_code(A.dtype), ctypes.c_void_p(C.data_ptr()),
+        _dtype_code(C.dtype), n, _prec(precision),
+        ctypes.c_void_p(ws.data_ptr() if ws is not None else 0), ws_bytes, _stream(A.device)),
+        "ptdr_decompose")
+    return C
+
+
+def compose(C: torch.Tensor, scale: float = 1.0, precision: str = "fp32", out_dtype=None,
+            out=None) -> torch.Tensor:
+    """A = scale * sum_P C[P] P (the inverse of decompose for scale = 1)."""
+    C = _cuda(C, "C")
+    n = _n_of(C.shape[0])
+    if out_dtype is None:
+        out_dtype = C.dtype
+    A = out if out is not None else torch.empty((1 << n, 1 << n), dtype=out_dtype, device=C.device)
+    ws_bytes = workspace_size("compose", n, A.dtype, C.dtype, precision)
+    ws = _workspace(ws_bytes, C.device) if ws_bytes else None
+    check(_lib.load().ptdr_compose(
+        ctypes.c_void_p(C.data_ptr()), _dtype_code(C.dtype), ctypes.c_void_p(A.data_ptr()),
+        _dtype_code(A.dtype), n, float(scale), _prec(precision),
+        ctypes.c_void_p(ws.data_ptr() if ws is not None else 0), ws_bytes, _stream(C.device)),
+        "ptdr_compose")
+    return A
+
+
+def structured_masks(n: int, s: int) -> np.ndarray:
+    """Masks reachable by a band matrix of half-width s (host computation)."""
+    lib = _lib.load()
+    cnt = ctypes.c_size_t(0)
+    check(lib.ptdr_structured_masks(n, s, None, ctypes.byref(cnt)), "ptdr_structured_masks")
+    out = np.zeros(cnt.value, np.uint64)
+    check(lib.ptdr_structured_masks(n, s, out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(cnt)),
+          "ptdr_structured_masks")
+    return out
+
+
+def decompose_structured(bands: torch.Tensor, s: int, masks=None, precision: str = "fp64",
+                         out_dtype=None, workspace=None, out=None) -> torch.Tensor:
+    """Coefficients of a band matrix on its reachable masks (rows follow ``masks``).
+
+    ``bands`` has shape (2s+1, 2^n) with bands[d+s, c] = A[c+d, c].
+    """
+    bands = _cuda(bands, "bands")
+    if bands.ndim != 2 or bands.shape[0] != 2 * s + 1:
+        raise ValueError("bands must have shape (2s+1, 2^n)")
+    n = _n_of(bands.shape[1])
+    h_masks = structured_masks(n, s) if masks is None else np.ascontiguousarray(masks, np.uint64)
+    if out_dtype is None:
+        out_dtype = bands.dtype if not bands.dtype.is_complex else (
+            torch.complex128 if precision == "fp64" else torch.complex64)
+    C = out if out is not None else torch.empty((len(h_masks), 1 << n), dtype=out_dtype,
+                                                device=bands.device)
+    lib = _lib.load()
+    hp = h_masks.ctypes.data_as(ctypes.c_void_p)
+    wsz = ctypes.c_size_t(0)
+    check(lib.ptdr_structured_workspace_size(n, s, hp, len(h_masks), _dtype_code(bands.dtype),
+                                             _dtype_code(C.dtype), _prec(precision),
+                                             ctypes.byref(wsz)), "ptdr_structured_workspace_size")
+    ws = workspace if workspace is not None else (_workspace(wsz.value, bands.device) if wsz.value else None)
+    check(lib.ptdr_decompose_structured(
+        ctypes.c_void_p(bands.data_ptr()), _dtype_code(bands.dtype), n, s,
+        hp, len(h_masks), ctypes.c_void_p(C.data_ptr()),
+        _dtype_code(C.dtype), _prec(precision),
+        ctypes.c_void_p(ws.data_ptr() if ws is not None else 0), wsz.value, _stream(bands.device)),
+        "ptdr_decompose_structured")
+    return C
+
+
+class BatchedPlan:
+    """Device-side pointer/size tables and workspace for ptdr_decompose_batched.
+
+    Built once per list of matrices; ``run()`` enqueues the persistent launch,
+    so a CUDA graph can capture it and replay it with new data in the same
+    buffers.
+    """
+
+    def __init__(self, As, Cs, precision: str = "fp32"):
+        if len(As) != len(Cs) or not As:
+            raise ValueError("need matching non-empty input/output lists")
+        dev = As[0].device
+        self.As, self.Cs = As, Cs
+        self.h_n = np.array([_n_of(a.shape[0]) for a in As], np.int32)
+        self.d_A = torch.tensor([a.data_ptr() for a in As], dtype=torch.int64, device=dev)
+        self.d_C = torch.tensor([c.data_ptr() for c in Cs], dtype=torch.int64, device=dev)
+        self.d_n = torch.from_numpy(self.h_n).to(dev)
+        self.a_t, self.c_t = _dtype_code(As[0].dtype), _dtype_code(Cs[0].dtype)
+        self.prec = _prec(precision)
+        wsz = ctypes.c_size_t(0)
+        check(_lib.load().ptdr_batched_workspace_size(
+            self.h_n.ctypes.data_as(ctypes.c_void_p), len(As), self.a_t, self.c_t, self.prec,
+            ctypes.byref(wsz)), "ptdr_batched_workspace_size")
+        self.ws = _workspace(wsz.value, dev)
+        self.ws_bytes = wsz.value
+        self.device = dev
+
+    def run(self):
+        check(_lib.load().ptdr_decompose_batched(
+            ctypes.c_void_p(self.d_A.data_ptr()), ctypes.c_void_p(self.d_C.data_ptr()),
+            ctypes.c_void_p(self.d_n.data_ptr()), self.h_n.ctypes.data_as(ctypes.c_void_p),
+            len(self.As), self.a_t, self.c_t, self.prec, ctypes.c_void_p(self.ws.data_ptr()),
+            self.ws_bytes, _stream(self.device)), "ptdr_decompose_batched")
+        return self.Cs
+
+
+def decompose_batched(As, precision: str = "fp32", out_dtype=torch.complex64):
+    """Decomposes a list of CUDA matrices of possibly different sizes in one launch."""
+    As = [_cuda(a, "A") for a in As]
+    Cs = [torch.empty_like(a, dtype=out_dtype) for a in As]
+    return BatchedPlan(As, Cs, precision).run()
+
+
+def last_device_status(device=None) -> int:
+    """Synchronises the current stream and returns (and clears) the device status word."""
+    dev = torch.device("cuda") if device is None else torch.device(device)
+    return _lib.load().ptdr_last_device_status(_stream(dev))
+
+
+class PtdrDecompose(torch.autograd.Function):
+    """c = decompose(A); backward is the adjoint 2^-n * compose(grad_c).
+
+    c_P = 2^-n <P, A> is linear in A, so the vector-Jacobian product of a
+    gradient g (PyTorch's convention for complex tensors) is
+    2^-n sum_P g_P P, i.e. ptdr_compose with scale = 2^-n.
+    """
+
+    @staticmethod
+    def forward(ctx, A, precision="fp64"):
+        ctx.precision = precision
+        ctx.a_dtype = A.dtype
+        return decompose(A, precision=precision, out_dtype=A.dtype)
+
+    @staticmethod
+    def backward(ctx, grad_c):
+        n = _n_of(grad_c.shape[0])
+        prec = "fp64" if ctx.precision == "fp64" else "fp32"
+        gA = compose(grad_c.contiguous(), scale=2.0 ** (-n), precision=prec, out_dtype=ctx.a_dtype)
+        return gA, None
+
+
+def decompose_autograd(A: torch.Tensor, precision: str = "fp64") -> torch.Tensor:
+    return PtdrDecompose.apply(A, precision)

@@ -1,0 +1,173 @@
+"""GPU parity of dense decompose/compose against the CPU oracle (configs 1, 2, 5)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+from helpers import TOL, dev, host, rel_err
+
+pytestmark = pytest.mark.gpu
+
+ptdr = pytest.importorskip("paper_2403_11644_gb300")
+
+
+def setup_module(_):
+    from paper_2403_11644_gb300 import build
+    build.build()
+
+
+def ref_full(A):
+    n = A.shape[0].bit_length() - 1
+    return oracle.direct(A) if n <= 8 else oracle.fwht(A)
+
+
+@pytest.mark.parametrize("n", range(1, 12))
+@pytest.mark.parametrize("prec,adt", [("fp64", np.complex128), ("fp32", np.complex64),
+                                      ("fp64", np.complex64), ("fp32", np.complex128)])
+def test_all_sizes(n, prec, adt):
+    A = workloads.dense(n, 1000 + n, dtype=adt)
+    C = host(ptdr.decompose(dev(A), precision=prec))
+    assert rel_err(C, ref_full(A)) <= TOL[prec]
+    assert ptdr.last_device_status() == 0
+
+
+@pytest.mark.parametrize("hermitian", [False, True])
+def test_config_dense_n6(hermitian):
+    """dense n=6 complex128, general and Hermitian, FP64 against every oracle route."""
+    A = workloads.dense(6, 106 if hermitian else 6, hermitian=hermitian)
+    C = host(ptdr.decompose(dev(A), precision="fp64"))
+    for ref in (oracle.brute(A), oracle.direct(A), oracle.tree(A)):
+        assert rel_err(C, ref) <= TOL["fp64"]
+    if hermitian:  # Thm 2: real coefficients
+        assert np.max(np.abs(C.imag)) <= TOL["fp64"] * np.max(np.abs(C))
+
+
+@pytest.mark.parametrize("hermitian", [False, True])
+@pytest.mark.parametrize("prec,adt", [("fp64", np.complex128), ("fp32", np.complex64),
+                                      ("fp64", np.complex64)])
+def test_config_dense_n12(hermitian, prec, adt):
+    """dense n=12, complex128/complex64, general/Hermitian, FP64 and FP32 paths."""
+    A = workloads.dense(12, 112 if hermitian else 12, dtype=adt, hermitian=hermitian)
+    C = host(ptdr.decompose(dev(A), precision=prec))
+    assert rel_err(C, oracle.fwht(A)) <= TOL[prec]
+    xs = workloads.sample_masks(12, 12, count=30)
+    assert rel_err(C[xs.astype(np.int64)], oracle.direct(A, xs=xs)) <= TOL[prec]
+    if hermitian:
+        assert np.max(np.abs(C.imag)) <= 2 * TOL[prec] * np.max(np.abs(C))
+
+
+@pytest.fixture(scope="module")
+def a14():
+    return workloads.dense_c64_direct(14, 14)
+
+
+@pytest.fixture(scope="module")
+def ref14(a14):
+    return oracle.fwht(a14)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_config_dense_n14(a14, ref14, prec):
+    """dense n=14 complex64: full output against the FWHT check, sampled rows against the direct trace."""
+    Ad = dev(a14)
+    out_dtype = torch.complex128 if prec == "fp64" else torch.complex64
+    C = host(ptdr.decompose(Ad, precision=prec, out_dtype=out_dtype))
+    assert rel_err(C, ref14) <= TOL[prec]
+    xs = workloads.sample_masks(14, 14, count=14)
+    assert rel_err(C[xs.astype(np.int64)], oracle.direct(a14, xs=xs)) <= TOL[prec]
+    assert ptdr.last_device_status() == 0
+
+
+def test_n14_fp64_into_c64_workspace_path(a14, ref14):
+    C = host(ptdr.decompose(dev(a14), precision="fp64", out_dtype=torch.complex64))
+    assert rel_err(C, ref14) <= 1e-6  # rounded to complex64 once at the end
+
+
+def test_n15_fp32_multipass():
+    A = workloads.dense_c64_direct(15, 15)
+    C = host(ptdr.decompose(dev(A), precision="fp32"))
+    xs = workloads.sample_masks(15, 15, count=6)
+    ref = oracle.fwht(A, xs=xs)
+    assert rel_err(C[xs.astype(np.int64)], ref) <= TOL["fp32"]
+
+
+@pytest.mark.parametrize("n", [1, 3, 6, 9, 12])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_round_trip(n, prec):
+    adt = np.complex128 if prec == "fp64" else np.complex64
+    A = workloads.dense(n, 2000 + n, dtype=adt)
+    Ad = dev(A)
+    C = ptdr.decompose(Ad, precision=prec, out_dtype=Ad.dtype)
+    B = host(ptdr.compose(C, precision=prec))
+    assert rel_err(B, A) <= TOL[prec] * 4
+
+
+@pytest.mark.parametrize("n", [1, 4, 7])
+def test_compose_matches_oracle(n):
+    rng = np.random.default_rng(n)
+    C = rng.standard_normal((2 ** n, 2 ** n)) + 1j * rng.standard_normal((2 ** n, 2 ** n))
+    for scale in (1.0, 2.0 ** -n):
+        got = host(ptdr.compose(dev(C), scale=scale, precision="fp64"))
+        assert rel_err(got, oracle.compose(C, scale=scale)) <= TOL["fp64"]
+
+
+def test_compose_multipass_n15():
+    rng = np.random.default_rng(15)
+    A = workloads.dense_c64_direct(15, 150)
+    Ad = dev(A)
+    C = ptdr.decompose(Ad, precision="fp32")
+    B = host(ptdr.compose(C, precision="fp32"))
+    assert rel_err(B, A) <= 4 * TOL["fp32"]
+
+
+def test_single_operator_inputs_exact():
+    import itertools
+    sig = {"I": np.eye(2), "X": np.array([[0, 1], [1, 0]]), "Y": np.array([[0, -1j], [1j, 0]]),
+           "Z": np.diag([1, -1])}
+    code = {"I": (0, 0), "X": (1, 0), "Y": (1, 1), "Z": (0, 1)}
+    n = 3
+    for s in itertools.product("IXYZ", repeat=n):
+        P = np.array([[1.0 + 0j]])
+        x = z = 0
+        for l, ch in enumerate(reversed(s)):
+            x |= code[ch][0] << l
+            z |= code[ch][1] << l
+        for ch in s:
+            P = np.kron(P, sig[ch])
+        C = host(ptdr.decompose(dev(P.astype(np.complex128)), precision="fp64"))
+        want = np.zeros((8, 8), complex)
+        want[x, z] = 1
+        assert np.array_equal(C, want), s
+
+
+def test_deterministic():
+    A = dev(workloads.dense(12, 77, dtype=np.complex64))
+    a = host(ptdr.decompose(A, precision="fp32"))
+    b = host(ptdr.decompose(A, precision="fp32"))
+    assert np.array_equal(a, b)
+
+
+def test_parseval_n12():
+    A = workloads.dense(12, 99)
+    C = host(ptdr.decompose(dev(A), precision="fp64"))
+    lhs = np.sum(np.abs(A) ** 2)
+    assert abs(lhs - 4096 * np.sum(np.abs(C) ** 2)) / lhs < 1e-13
+
+
+def test_checked_build_small():
+    """Bounds-checked build: same results, and the status word stays clean."""
+    import ctypes
+    from paper_2403_11644_gb300 import _lib, build
+    build.build(checked=True)
+    L = _lib.load(checked=True)
+    for n in (3, 8, 15):
+        A = dev(workloads.dense(n, 5, dtype=np.complex64) if n < 15 else workloads.dense_c64_direct(15, 5))
+        C = torch.empty_like(A)
+        st = L.ptdr_decompose(ctypes.c_void_p(A.data_ptr()), _lib.C64, ctypes.c_void_p(C.data_ptr()),
+                              _lib.C64, n, _lib.PREC_FP32, None, 0,
+                              ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        assert st == 0
+        assert L.ptdr_last_device_status(ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)) == 0
+        ref = host(ptdr.decompose(A, precision="fp32"))
+        assert np.array_equal(host(C), ref)

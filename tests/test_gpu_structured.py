@@ -35,11 +35,15 @@ def test_general_complex_bands(n, s, prec):
 def test_unreachable_and_repeated_masks_give_oracle_rows():
     n, s = 8, 2
     bands = workloads.random_bands(n, s, seed=7)
-    masks = np.array([5, 0, 255, 3, 3, 128], np.uint64)  # 5, 255 and 128 are out of the band's reach
+    # 5 (2^2 - 1 = 3 > s) and 128 (2^7 - 0 > s) are out of the band's reach; 255 is reachable
+    masks = np.array([5, 0, 255, 3, 3, 128], np.uint64)
+    reach = set(oracle.band_masks(n, s).tolist())
+    assert 5 not in reach and 128 not in reach and 255 in reach
     C = host(ptdr.decompose_structured(dev(bands), s, masks=masks, precision="fp64"))
     ref = oracle.band_direct(bands, s, masks)
     assert rel_err(C, ref) <= TOL["fp64"]
-    assert np.max(np.abs(C[0])) == 0 and np.max(np.abs(C[2])) == 0
+    assert np.max(np.abs(C[0])) == 0 and np.max(np.abs(C[5])) == 0
+    assert np.array_equal(C[3], C[4])
 
 
 @pytest.mark.parametrize("n", [9, 12])

@@ -41,6 +41,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra-paths", action="store_true")
+    ap.add_argument("--n", type=int, default=14, help="matrix size 2^n (profiling of smaller cases)")
     return ap.parse_args()
 
 
@@ -181,9 +182,11 @@ def main():
     from paper_2403_11644_gb300 import build as lib_build
 
     lib_build.build()
+    global N_QUBITS
+    N_QUBITS = args.n
     prec = args.precision or "fp32"
     out_dtype = torch.complex128 if prec == "fp64" else torch.complex64
-    A_h = workloads.dense_c64_direct(N_QUBITS, SEED + rank)
+    A_h = workloads.dense_c64_direct(N_QUBITS, (SEED if N_QUBITS == 14 else N_QUBITS) + rank)
     A = torch.from_numpy(A_h).to(dev)
     C = torch.empty((1 << N_QUBITS, 1 << N_QUBITS), dtype=out_dtype, device=dev)
     ncoef = 1 << (2 * N_QUBITS)
@@ -242,7 +245,8 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp32": "f32", "fp64": "f64", "bf16x3": "bf16x3->f32", "fp16x2": "fp16x2->f32"}[prec],
             "data": "synthetic",
-            "config": {"workload": "dense n=14 16384x16384 complex64 N(0,1), seed 14 (+rank)",
+            "config": {"workload": f"dense n={N_QUBITS} {1 << N_QUBITS}x{1 << N_QUBITS} complex64 N(0,1), "
+                                   f"seed {SEED if N_QUBITS == 14 else N_QUBITS} (+rank)",
                        "n": N_QUBITS, "precision": prec, "output": str(out_dtype).split(".")[-1],
                        "l2": "inputs larger than L2 (2 GiB in, 2 GiB out), no flush",
                        "parallelism": f"replicas x{world}"},
@@ -310,7 +314,7 @@ def main():
                 extra[p2] = {"error": str(e)}
         result["paths"] = extra
 
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and N_QUBITS == 14 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline()
 
     if rank == 0:

@@ -196,6 +196,35 @@ ptdr_status ptdr_batched_workspace_size(const int* h_n, int count, ptdr_dtype a_
                                         ptdr_dtype c_type, ptdr_precision prec, size_t* bytes);
 
 /*
+ * ptdr_decompose_batched_static -- ptdr_decompose_batched for callers that
+ * cannot allocate device memory.  The paper has no counterpart: this is a
+ * library convenience, not part of the method.
+ *
+ * Who needs it: an application that embeds this library but owns all device
+ * memory through its own pool, code that runs during a CUDA graph capture or
+ * on a latency-critical stream where an allocation would synchronise the
+ * device, or a runtime that forbids allocations after start-up.  Such a caller
+ * cannot provide the workspace ptdr_decompose_batched asks for.  This variant
+ * allocates nothing: its scratch is a fixed 32,784-byte array in the library's
+ * device image (every GPU that loads the library holds it until exit).
+ *
+ *   Arguments as for ptdr_decompose_batched, without the workspace.
+ *   count      at most 4096 matrices; larger batches return
+ *              PTDR_ERR_WORKSPACE (use ptdr_decompose_batched instead).
+ *   The first call on each device looks up the array's device address (with
+ *   that device current) and caches it; make that first call before any
+ *   stream capture.  Every call shares the one array, which keeps the last
+ *   call's tables; each call rewrites all of it (including the work-queue
+ *   counter) before use, so results never depend on an earlier call, but two
+ *   calls whose work overlaps on the GPU (different streams, or different
+ *   host threads without ordering) race on it and must not be issued.
+ */
+ptdr_status ptdr_decompose_batched_static(const void* const* d_A, void* const* d_C,
+                                          const int* d_n, const int* h_n, int count,
+                                          ptdr_dtype a_type, ptdr_dtype c_type,
+                                          ptdr_precision prec, void* stream);
+
+/*
  * ptdr_last_device_status -- synchronises `stream`, returns the status word
  * the kernels wrote since the previous call (PTDR_OK if none) and clears it.
  */

@@ -41,6 +41,7 @@ SIGNATURES = {
     "ptdr_structured_workspace_size": [_i, _i, _vp, _sz, _i, _i, _i, _szp],
     "ptdr_decompose_batched": [_vp, _vp, _vp, _vp, _i, _i, _i, _i, _vp, _sz, _vp],
     "ptdr_batched_workspace_size": [_vp, _i, _i, _i, _i, _szp],
+    "ptdr_decompose_batched_static": [_vp, _vp, _vp, _vp, _i, _i, _i, _i, _vp],
     "ptdr_last_device_status": [_vp],
     "ptdr_status_string": [_i],
     "ptdr_version": [],

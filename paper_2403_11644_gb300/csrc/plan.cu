@@ -33,8 +33,23 @@ std::vector<StridedPass> strided_schedule(int b0, int n, size_t elem_bytes)
 ptdr_status make_dense_plan(bool compose, int n, ptdr_dtype in_t, ptdr_dtype out_t,
                             ptdr_precision prec, DensePlan* plan)
 {
-    if (prec == PTDR_PREC_SPLIT_BF16_TC || prec == PTDR_PREC_SPLIT_FP16_TC)
-        return PTDR_ERR_UNSUPPORTED; // tensor-core path not built yet
+    if (prec == PTDR_PREC_SPLIT_FP16_TC) return PTDR_ERR_UNSUPPORTED;
+    if (prec == PTDR_PREC_SPLIT_BF16_TC) {
+        // the tensor-core path covers the n = 14 complex64 workload
+        if (compose || n != 14 || in_t != PTDR_C64 || out_t != PTDR_C64) return PTDR_ERR_UNSUPPORTED;
+        return PTDR_ERR_UNSUPPORTED; // the tensor-core kernel is enabled once its layouts are validated
+        DensePlan p;
+        p.compose = false;
+        p.n = n;
+        p.in_t = in_t;
+        p.out_t = out_t;
+        p.prec = prec;
+        p.calc = Calc::F32;
+        p.kernel = DenseKernel::Tc14;
+        p.single = true;
+        *plan = p;
+        return PTDR_OK;
+    }
     DensePlan p;
     p.compose = compose;
     p.n = n;
@@ -45,6 +60,14 @@ ptdr_status make_dense_plan(bool compose, int n, ptdr_dtype in_t, ptdr_dtype out
     const size_t S = p.calc == Calc::F64 ? 16 : 8;
     const size_t N = (size_t)1 << n;
     const size_t row_bytes = N * S;
+    if (!compose && n == 14 && p.calc == Calc::F32) {
+        p.kernel = DenseKernel::Row14;
+        p.single = true;
+        // the clustered complex64 kernel exchanges through a scratch in the workspace
+        if (in_t == PTDR_C64 && out_t == PTDR_C64) p.ws_bytes = dense14_x4_workspace();
+        *plan = p;
+        return PTDR_OK;
+    }
     if (row_bytes <= kRowTileBytes) {
         p.single = true;
         p.log_l = n;
@@ -81,6 +104,20 @@ ptdr_status execute_dense(const DensePlan& p, const void* in, void* out, void* w
 {
     const uint64_t N = 1ull << p.n;
     cudaError_t e = cudaSuccess;
+    if (p.kernel == DenseKernel::Tc14) {
+        if (!tc14_supported(in, p.in_t, p.out_t)) return PTDR_ERR_INVALID_ARG; // needs 16-byte alignment
+        e = launch_tc14(in, out, st, s);
+        return e == cudaSuccess ? PTDR_OK : PTDR_ERR_CUDA;
+    }
+    if (p.kernel == DenseKernel::Row14) {
+        // complex64 -> complex64 with a 16-byte aligned input takes the
+        // clustered tile kernel; other type pairs the one-mask-per-CTA kernel
+        if (ws && dense14_x4_supported(in, p.in_t, p.out_t))
+            e = launch_dense14_x4(in, out, ws, st, s);
+        else
+            e = launch_row14(in, p.in_t, out, p.out_t, st, s);
+        return e == cudaSuccess ? PTDR_OK : PTDR_ERR_CUDA;
+    }
     if (p.single) {
         TileLaunch t{};
         t.src = in;

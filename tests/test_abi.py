@@ -89,7 +89,11 @@ def ws_size(lib, op, n, a, c, p):
 def test_workspace_sizes(lib):
     C64, C128 = _lib.C64, _lib.C128
     assert ws_size(lib, 0, 12, C64, C64, _lib.PREC_FP32) == (OK, 0)
-    assert ws_size(lib, 0, 14, C64, C64, _lib.PREC_FP32) == (OK, 0)
+    st, b = ws_size(lib, 0, 14, C64, C64, _lib.PREC_FP32)  # clustered kernel's exchange scratch
+    assert st == OK and 0 < b <= 128 << 20
+    assert ws_size(lib, 0, 14, C128, C64, _lib.PREC_FP32) == (OK, 0)
+    assert ws_size(lib, 0, 12, C64, C64, _lib.PREC_SPLIT_BF16_TC)[0] == UNSUPPORTED
+    assert ws_size(lib, 0, 14, C64, C64, _lib.PREC_SPLIT_FP16_TC)[0] == UNSUPPORTED
     assert ws_size(lib, 0, 15, C64, C64, _lib.PREC_FP32) == (OK, 0)  # intermediate in C
     st, b = ws_size(lib, 0, 14, C64, C64, _lib.PREC_FP64)  # FP64 intermediate, C64 out
     assert st == OK and b > 0

@@ -42,13 +42,15 @@ constexpr int kN = 1 << kLog;
 constexpr int kThreads = 512;
 constexpr int kXBlocks = kN / 4;
 constexpr int kMaxClusters = 64;            // scratch is sized for this many resident clusters
-constexpr int kMainElems = 16896;          // float2: tiles, then the round-1 layout
+constexpr int kS1 = 4228;                  // mask row stride of the round-1 layout (float2)
+constexpr int kMainElems = 4 * kS1;        // float2: tiles, then the round-1 layout
 constexpr int kBufBytes = (kMainElems + 4096) * 8 + 128; // + own quarter + alignment slack
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ int pad32(int k) { return k + (k >> 5); }
-// layout after round 1: [k_loc][mask] interleaved, one pad element per 32
-__device__ __forceinline__ int w1(int kloc, int m) { return pad32(kloc * 4 + m); }
+// layout after round 1: [mask][k_loc], one pad element per 32 and a mask row
+// stride that keeps round 1's stores and round 2's loads at two wavefronts
+__device__ __forceinline__ int w1(int m, int kloc) { return m * kS1 + pad32(kloc); }
 
 __device__ __forceinline__ uint32_t cluster_rank()
 {
@@ -141,25 +143,26 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (__popc(z & c) & 1) v[z] = make_float2(-v[z].x, -v[z].y);
             __syncthreads();
 #pragma unroll
-            for (int z = 0; z < 32; ++z) buf[w1(32 * g + z, m)] = v[z];
+            for (int z = 0; z < 32; ++z) buf[w1(m, 32 * g + z)] = v[z];
         }
         __syncthreads();
 
-        // ---- round 2: k_loc bits 5-9.  Once every thread holds its values the
-        // buffer is free and the next x-block's gather starts underneath.
-        const int h = (lane >> 2) | (warp << 3);
-        const int kbase = (h & 31) | ((h >> 5) << 10);
+        // ---- round 2: k_loc bits 5-9, one mask per warp.  Once every thread
+        // holds its values the buffer is free and the next x-block's gather
+        // starts underneath.
+        const int m2 = warp & 3;
+        const int kbase = lane | ((warp >> 2) << 10);
 #pragma unroll
-        for (int s = 0; s < 32; ++s) v[s] = buf[w1(kbase | (s << 5), m)];
+        for (int s = 0; s < 32; ++s) v[s] = buf[w1(m2, kbase | (s << 5))];
         __syncthreads();
         if (xb + (uint32_t)nclusters < (uint32_t)kXBlocks)
             gather_slice(A, buf_a, rank, xb + (uint32_t)nclusters, t, st);
         wht_regs<5>(v);
-        float2* out_q = my_scratch + ((size_t)((it & 1u) * 4u + rank) * 4u + (uint32_t)m) * 4096u;
-        if ((uint32_t)m == rank) {
+        if ((uint32_t)m2 == rank) {
 #pragma unroll
             for (int s = 0; s < 32; ++s) loc[kbase | (s << 5)] = v[s];
         } else {
+            float2* out_q = my_scratch + ((size_t)((it & 1u) * 4u + rank) * 4u + (uint32_t)m2) * 4096u;
 #pragma unroll
             for (int s = 0; s < 32; ++s) __stcg(out_q + (kbase | (s << 5)), v[s]);
         }
@@ -169,27 +172,31 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint64_t x = 4ull * xb + rank;
         float2* row = C + (x << kLog);
         const float2* in_base = my_scratch + (size_t)((it & 1u) * 16u + rank) * 4096u; // [src = 0][mask = rank]
+        float2 e[2][16];
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            const int zp = t + 512 * half;
-            float2 e[16];
+        for (int half = 0; half < 2; ++half)
 #pragma unroll
             for (int src = 0; src < 4; ++src)
 #pragma unroll
                 for (int c2 = 0; c2 < 4; ++c2) {
-                    const int kl = (c2 << 10) | zp;
-                    e[c2 | (src << 2)] = ((uint32_t)src == rank) ? loc[kl] : __ldcg(in_base + src * 4 * 4096 + kl);
+                    const int kl = (c2 << 10) | (t + 512 * half);
+                    e[half][c2 | (src << 2)] =
+                        ((uint32_t)src == rank) ? loc[kl] : __ldcg(in_base + src * 4 * 4096 + kl);
                 }
-            wht_regs<4>(e);
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const int zp = t + 512 * half;
+            wht_regs<4>(e[half]);
 #pragma unroll
             for (int f = 0; f < 16; ++f) {
                 const uint64_t z = (uint64_t)(zp | (f << 10));
+                const float2 w = e[half][f];
                 float2 o;
                 switch (__popcll(x & z) & 3) {
-                case 0: o = make_float2(e[f].x, e[f].y); break;
-                case 1: o = make_float2(e[f].y, -e[f].x); break;
-                case 2: o = make_float2(-e[f].x, -e[f].y); break;
-                default: o = make_float2(-e[f].y, e[f].x); break;
+                case 0: o = make_float2(w.x, w.y); break;
+                case 1: o = make_float2(w.y, -w.x); break;
+                case 2: o = make_float2(-w.x, -w.y); break;
+                default: o = make_float2(-w.y, w.x); break;
                 }
                 o.x *= scale;
                 o.y *= scale;

@@ -1,0 +1,282 @@
+// Dense n = 14 decomposition, complex64 -> complex64, FP32 arithmetic, as two
+// passes over an L2-resident staging buffer with contiguous HBM traffic.
+//
+// The XOR shear d_x[k] = A[k ^ x][k] maps 128 x 128 tiles onto 128 x 128
+// tiles: with x = 128 xt + xl and k = 128 cb + cl, the entries of masks
+// x in x-tile xt and columns k in column block cb are A[128 (cb ^ xt) + (cl ^ xl)]
+// [128 cb + cl], all inside the one tile (R = cb ^ xt, cb) of A, permuted by
+// cl ^ xl.  The length-2^14 transform over k splits into 7 bits inside the
+// column block (cl) and 7 bits across blocks (cb):
+//   pass 1 (tile item):  load the A tile with contiguous 1 KiB rows, transform
+//            over cl for its 128 masks, write D'[xl][128 cb + zl] to the
+//            staging slot of x-tile xt (16 MiB, stays in L2);
+//   pass 2 (row item):   read the staging row of one mask x (128 KiB from L2),
+//            transform over cb, apply (-i)^{|x&z|} and 2^-14, write C[x][.]
+//            with contiguous stores, and discard the staging lines so the
+//            dead intermediate is never written back to HBM.
+// HBM sees A read once and C written once, both in whole 1 KiB rows, instead
+// of 32-byte pieces from rows 128 KiB apart.
+//
+// Work items are halves (64 KiB each) so that two CTAs share an SM and one
+// CTA's loads overlap the other's arithmetic: a half-tile item covers 64 of
+// the tile's 128 masks, a half-row item 64 of a row's 128 z_lo values.
+//
+// One persistent kernel runs both passes from an atomic work queue.  The
+// queue order is x-tile major with one tile of look-ahead: round r holds the
+// 256 half-tile items of x-tile r, then the 256 half-row items of x-tile r-1.
+// A half-row item waits (bounded) until its x-tile's 256 half-tile items are
+// done; a half-tile item of x-tile c waits (bounded) before writing until
+// x-tile c-2 has been read out of the same staging slot.  Every item waited
+// on was dequeued earlier by a running CTA, so the waits always end.
+#include <mutex>
+
+#include "common.cuh"
+#include "plan.h"
+
+namespace ptdr {
+
+namespace {
+
+constexpr int kLog = 14;
+constexpr int kN = 1 << kLog;
+constexpr int kT = 128;                     // tile edge / masks per x-tile
+constexpr int kH = 64;                      // half tile: masks (pass 1) or z_lo values (pass 2) per item
+constexpr int kTiles = kN / kT;             // 128 x-tiles, 128 column blocks
+constexpr int kThreads = 256;
+constexpr int kSlots = 2;                   // staging slots (x-tiles in flight)
+constexpr int kYaStride = 129;              // pass 1 transpose: 64 rows x 128, padded (float2)
+constexpr int kYbStride = 65;               // pass 2 transpose: 128 rows x 64, padded (float2)
+constexpr int kSmemElems = kT * kYbStride;  // 8320 float2 >= 128 x 64 tile and 64 x 129
+constexpr int kSmemBytes = kSmemElems * 8 + 128;
+constexpr long long kSpinLimit = 1ll << 24;
+constexpr int kPerRound = 4 * kT;           // 256 half-tile items + 256 half-row items
+constexpr int kItems = (kTiles + 1) * kPerRound;
+constexpr int kDone = 2 * kT;               // items per x-tile and pass
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+template <int NB>
+__device__ __forceinline__ void wht_regs(float2 (&v)[1 << NB])
+{
+#pragma unroll
+    for (int h = 1; h < (1 << NB); h <<= 1)
+#pragma unroll
+        for (int i = 0; i < (1 << NB); ++i)
+            if (!(i & h)) {
+                float2 a = v[i], b = v[i + h];
+                v[i] = make_float2(a.x + b.x, a.y + b.y);
+                v[i + h] = make_float2(a.x - b.x, a.y - b.y);
+            }
+}
+
+__device__ __forceinline__ int ld_acquire(const int* p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Bounded wait by thread 0 for *p >= target; records a timeout and gives up.
+__device__ __forceinline__ void wait_count(const int* p, int target, unsigned int* st)
+{
+    long long spins = 0;
+    while (ld_acquire(p) < target) {
+        if (++spins > kSpinLimit) {
+            report_status(st, PTDR_ERR_TIMEOUT);
+            return;
+        }
+        __nanosleep(64);
+    }
+}
+
+} // namespace
+
+struct StagedTables {
+    int* head;  // work-queue counter
+    int* done1; // tile items finished per x-tile
+    int* done2; // row items finished per x-tile
+    float2* stage; // kSlots x 128 rows x 2^14
+};
+
+__global__ void __launch_bounds__(kThreads, 2)
+    k_dense14_staged(const float2* __restrict__ A, float2* __restrict__ C, StagedTables tab, unsigned int* st)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ int s_item;
+    const uint32_t raw_a = su32(smem_raw);
+    const uint32_t buf_a = (raw_a + 127u) & ~127u;
+    float2* buf = reinterpret_cast<float2*>(smem_raw + (buf_a - raw_a));
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const float scale = 1.0f / (float)kN;
+
+    for (;;) {
+        if (t == 0) s_item = atomicAdd(tab.head, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= kItems) break;
+        const int r = item / kPerRound, j = item % kPerRound;
+
+        if (j < 2 * kT) {
+            // ------------------------------------------------ half-tile item
+            // masks xl in [64 h, 64 h + 64) of x-tile xt, column block cb.
+            // Row rl of the A tile contributes columns cl with cl bit 6 =
+            // (rl bit 6) ^ h: one contiguous 512-byte run per row.
+            const int xt = r, cb = j >> 1, h = j & 1;
+            if (xt >= kTiles) { __syncthreads(); continue; }
+            const int R = cb ^ xt;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int qc = t + kThreads * i; // 16-byte chunk: row qc >> 5, pair qc & 31
+                const int rl = qc >> 5;
+                const int b = ((rl >> 6) ^ h) & 1;
+                const uint64_t gi = ((uint64_t)(kT * R + rl) << kLog) + (uint64_t)(kT * cb + kH * b) + 2u * (qc & 31);
+                const float2* src = A + (in_bounds(st, gi + 1, (uint64_t)kN * kN) ? gi : 0);
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(buf_a + (uint32_t)qc * 16u), "l"(src)
+                             : "memory");
+            }
+            asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+            __syncthreads();
+            // round a: cl bits 0-4.  Lane l of warp w handles mask xl = 64 h + 32 (w & 1) + l
+            // and column group g = w >> 1; at step s it reads cl = 32 g + (s ^ l), so all
+            // lanes read the same tile row at distinct columns; the register transform
+            // then carries the sign (-1)^{|z & l|}.
+            const int xloc = 32 * (warp & 1) + lane, xl = kH * h + xloc, g = warp >> 1;
+            float2 v[32];
+#pragma unroll
+            for (int s = 0; s < 32; ++s) {
+                const int cl = 32 * g + (s ^ lane);
+                v[s] = buf[(cl ^ xl) * kH + (cl & (kH - 1))];
+            }
+            wht_regs<5>(v);
+#pragma unroll
+            for (int z = 0; z < 32; ++z)
+                if (__popc(z & lane) & 1) v[z] = make_float2(-v[z].x, -v[z].y);
+            __syncthreads();
+#pragma unroll
+            for (int z = 0; z < 32; ++z) buf[xloc * kYaStride + 32 * g + z] = v[z];
+            __syncthreads();
+            // round b: cl bits 5-6; lane = z5, rows 8 w + i of the half tile
+            if (t == 0 && xt >= kSlots) wait_count(tab.done2 + (xt - kSlots), kDone, st);
+            __syncthreads();
+            float2* stage = tab.stage + ((size_t)(xt % kSlots) * kT + kH * h) * kN;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int row = 8 * warp + i;
+                float2 e[4];
+#pragma unroll
+                for (int gg = 0; gg < 4; ++gg) e[gg] = buf[row * kYaStride + 32 * gg + lane];
+                wht_regs<2>(e);
+#pragma unroll
+                for (int gg = 0; gg < 4; ++gg)
+                    __stcg(stage + (size_t)row * kN + kT * cb + 32 * gg + lane, e[gg]);
+            }
+            __syncthreads();
+            if (t == 0) {
+                __threadfence();
+                atomicAdd(tab.done1 + xt, 1);
+            }
+        } else {
+            // ------------------------------------------------ half-row item
+            // mask xl of x-tile xt, output columns z_lo in [64 h, 64 h + 64)
+            const int jj = j - 2 * kT;
+            const int xt = r - 1, xl = jj >> 1, h = jj & 1;
+            if (xt < 0) { __syncthreads(); continue; }
+            if (t == 0) wait_count(tab.done1 + xt, kDone, st);
+            __syncthreads();
+            const uint64_t x = (uint64_t)(kT * xt + xl);
+            const float2* srow = tab.stage + ((size_t)(xt % kSlots) * kT + xl) * kN + kH * h;
+            // round a: cb bits 0-4; lanes take consecutive z_lo (coalesced L2 reads)
+            const int zloc = 32 * (warp & 1) + lane, q = warp >> 1;
+            float2 v[32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i) v[i] = __ldcg(srow + (size_t)(32 * q + i) * kT + zloc);
+            wht_regs<5>(v);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) buf[(32 * q + i) * kYbStride + zloc] = v[i];
+            __syncthreads();
+            // this item's half of the staging row is consumed: drop its lines from
+            // L2 without write-back (4 lines of 128 bytes per column block)
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int ln = t + kThreads * i; // 512 lines
+                const float2* p = srow + (size_t)(ln >> 2) * kT + 16 * (ln & 3);
+                asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
+            }
+            // round b: cb bits 5-6, then phase, scale and contiguous stores
+            float2* out = C + (x << kLog) + kH * h;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int c5 = 8 * q + i;
+                float2 e[4];
+#pragma unroll
+                for (int gg = 0; gg < 4; ++gg) e[gg] = buf[(32 * gg + c5) * kYbStride + zloc];
+                wht_regs<2>(e);
+#pragma unroll
+                for (int gg = 0; gg < 4; ++gg) {
+                    const uint64_t zoff = (uint64_t)(kT * (32 * gg + c5) + zloc);
+                    const uint64_t z = zoff + (uint64_t)(kH * h);
+                    const float2 w = e[gg];
+                    float2 o;
+                    switch (__popcll(x & z) & 3) {
+                    case 0: o = make_float2(w.x, w.y); break;
+                    case 1: o = make_float2(w.y, -w.x); break;
+                    case 2: o = make_float2(-w.x, -w.y); break;
+                    default: o = make_float2(-w.y, w.x); break;
+                    }
+                    o.x *= scale;
+                    o.y *= scale;
+                    if (in_bounds(st, (x << kLog) + z, (uint64_t)kN * kN)) __stcs(out + zoff, o);
+                }
+            }
+            __syncthreads();
+            if (t == 0) {
+                __threadfence();
+                atomicAdd(tab.done2 + xt, 1);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ host
+
+size_t dense14_staged_workspace()
+{
+    // counters (head, done1[128], done2[128]) padded to 4 KiB, then the slots
+    return 4096 + (size_t)kSlots * kT * kN * sizeof(float2);
+}
+
+cudaError_t launch_dense14_staged(const void* A, void* C, void* ws, unsigned int* st, cudaStream_t s)
+{
+    static std::mutex mu;
+    static int grid_for[128];
+    cudaError_t e = cudaFuncSetAttribute(k_dense14_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    if (e != cudaSuccess) return e;
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    int grid = 0;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        grid = grid_for[dev & 127];
+    }
+    if (grid == 0) {
+        int sms = 0, per = 0;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_dense14_staged, kThreads, kSmemBytes)) !=
+            cudaSuccess)
+            return e;
+        grid = sms * (per > 0 ? per : 1);
+        std::lock_guard<std::mutex> lk(mu);
+        grid_for[dev & 127] = grid;
+    }
+    char* w = (char*)ws;
+    StagedTables tab;
+    tab.head = (int*)w;
+    tab.done1 = (int*)(w + 64);
+    tab.done2 = (int*)(w + 64 + 4 * kTiles);
+    tab.stage = (float2*)(w + 4096);
+    if ((e = cudaMemsetAsync(ws, 0, 4096, s)) != cudaSuccess) return e;
+    k_dense14_staged<<<grid, kThreads, kSmemBytes, s>>>((const float2*)A, (float2*)C, tab, st);
+    return cudaGetLastError();
+}
+
+} // namespace ptdr

@@ -64,7 +64,8 @@ ptdr_status make_dense_plan(bool compose, int n, ptdr_dtype in_t, ptdr_dtype out
         p.kernel = DenseKernel::Row14;
         p.single = true;
         // the clustered complex64 kernel exchanges through a scratch in the workspace
-        if (in_t == PTDR_C64 && out_t == PTDR_C64) p.ws_bytes = dense14_x4_workspace();
+        if (in_t == PTDR_C64 && out_t == PTDR_C64)
+            p.ws_bytes = std::max(dense14_x4_workspace(), dense14_staged_workspace());
         *plan = p;
         return PTDR_OK;
     }
@@ -113,7 +114,7 @@ ptdr_status execute_dense(const DensePlan& p, const void* in, void* out, void* w
         // complex64 -> complex64 with a 16-byte aligned input takes the
         // clustered tile kernel; other type pairs the one-mask-per-CTA kernel
         if (ws && dense14_x4_supported(in, p.in_t, p.out_t))
-            e = launch_dense14_x4(in, out, ws, st, s);
+            e = launch_dense14_staged(in, out, ws, st, s);
         else
             e = launch_row14(in, p.in_t, out, p.out_t, st, s);
         return e == cudaSuccess ? PTDR_OK : PTDR_ERR_CUDA;

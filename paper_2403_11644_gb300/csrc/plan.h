@@ -57,6 +57,8 @@ bool tc14_supported(const void* A, ptdr_dtype a_t, ptdr_dtype c_t);
 cudaError_t launch_tc14(const void* A, void* C, unsigned int* status, cudaStream_t s);
 cudaError_t launch_dense14_x4(const void* A, void* C, void* ws, unsigned int* status, cudaStream_t s);
 size_t dense14_x4_workspace();
+cudaError_t launch_dense14_staged(const void* A, void* C, void* ws, unsigned int* status, cudaStream_t s);
+size_t dense14_staged_workspace();
 
 // shared helpers (ptdr_api.cu)
 ptdr_status device_ready(int* dev);

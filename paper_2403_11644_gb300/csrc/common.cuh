@@ -46,20 +46,21 @@ template <typename T2> __device__ __forceinline__ T2 csub(T2 a, T2 b)
     return a;
 }
 
-// Multiply by (-i)^p (p taken mod 4) and by a real scale: a swap of the real
-// and imaginary parts plus signs; no complex multiply.
+// Multiply by (-i)^p (p taken mod 4) and by a real scale without a complex
+// multiply or a branch: an odd p swaps the real and imaginary parts, the real
+// part changes sign for p = 2, 3 and the imaginary part for p = 1, 2.  (Lanes
+// of a warp hold different p, so a switch here would diverge four ways.)
 template <typename T2, typename T>
 __device__ __forceinline__ T2 phase_neg_i(T2 v, int p, T s)
 {
+    const bool odd = (p & 1) != 0;
+    const T u = odd ? v.y : v.x;
+    const T w = odd ? v.x : v.y;
+    const T sr = (p & 2) ? -s : s;
+    const T si = ((p ^ (p >> 1)) & 1) ? -s : s;
     T2 r;
-    switch (p & 3) {
-    case 0: r.x = v.x; r.y = v.y; break;     // 1
-    case 1: r.x = v.y; r.y = -v.x; break;    // -i
-    case 2: r.x = -v.x; r.y = -v.y; break;   // -1
-    default: r.x = -v.y; r.y = v.x; break;   // +i
-    }
-    r.x *= s;
-    r.y *= s;
+    r.x = u * sr;
+    r.y = w * si;
     return r;
 }
 

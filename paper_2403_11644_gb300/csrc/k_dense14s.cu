@@ -43,7 +43,7 @@ constexpr int kT = 128;                     // tile edge / masks per x-tile
 constexpr int kH = 64;                      // half tile: masks (pass 1) or z_lo values (pass 2) per item
 constexpr int kTiles = kN / kT;             // 128 x-tiles, 128 column blocks
 constexpr int kThreads = 256;
-constexpr int kSlots = 2;                   // staging slots (x-tiles in flight)
+constexpr int kSlots = 4;                   // staging slots (x-tiles in flight)
 constexpr int kYaStride = 129;              // pass 1 transpose: 64 rows x 128, padded (float2)
 constexpr int kYbStride = 65;               // pass 2 transpose: 128 rows x 64, padded (float2)
 constexpr int kSmemElems = kT * kYbStride;  // 8320 float2 >= 128 x 64 tile and 64 x 129
@@ -109,8 +109,16 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const float scale = 1.0f / (float)kN;
 
+    // thread 0 keeps the next item in hand so the queue's atomic latency
+    // overlaps the current item (a held item is always later in the queue
+    // than the one being processed, so the dependency waits still end)
+    int next = 0;
+    if (t == 0) next = atomicAdd(tab.head, 1);
     for (;;) {
-        if (t == 0) s_item = atomicAdd(tab.head, 1);
+        if (t == 0) {
+            s_item = next;
+            if (next < kItems) next = atomicAdd(tab.head, 1);
+        }
         __syncthreads();
         const int item = s_item;
         if (item >= kItems) break;
@@ -216,15 +224,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                     const uint64_t zoff = (uint64_t)(kT * (32 * gg + c5) + zloc);
                     const uint64_t z = zoff + (uint64_t)(kH * h);
                     const float2 w = e[gg];
-                    float2 o;
-                    switch (__popcll(x & z) & 3) {
-                    case 0: o = make_float2(w.x, w.y); break;
-                    case 1: o = make_float2(w.y, -w.x); break;
-                    case 2: o = make_float2(-w.x, -w.y); break;
-                    default: o = make_float2(-w.y, w.x); break;
-                    }
-                    o.x *= scale;
-                    o.y *= scale;
+                    const float2 o = phase_neg_i(w, (int)(__popcll(x & z) & 3), scale);
                     if (in_bounds(st, (x << kLog) + z, (uint64_t)kN * kN)) __stcs(out + zoff, o);
                 }
             }

@@ -109,16 +109,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
             const uint64_t z = (uint64_t)(q + 1024 * j);
-            const int p = __popcll(x & z) & 3;
-            float2 c;
-            switch (p) {
-            case 0: c = make_float2(w[j].x, w[j].y); break;
-            case 1: c = make_float2(w[j].y, -w[j].x); break;
-            case 2: c = make_float2(-w[j].x, -w[j].y); break;
-            default: c = make_float2(-w[j].y, w[j].x); break;
-            }
-            c.x *= scale;
-            c.y *= scale;
+            const float2 c = phase_neg_i(w[j], (int)(__popcll(x & z) & 3), scale);
             if (in_bounds(st, (x << kLog) + z, lim)) st_out(row + z, c);
         }
     }

@@ -37,7 +37,6 @@ ptdr_status make_dense_plan(bool compose, int n, ptdr_dtype in_t, ptdr_dtype out
     if (prec == PTDR_PREC_SPLIT_BF16_TC) {
         // the tensor-core path covers the n = 14 complex64 workload
         if (compose || n != 14 || in_t != PTDR_C64 || out_t != PTDR_C64) return PTDR_ERR_UNSUPPORTED;
-        return PTDR_ERR_UNSUPPORTED; // the tensor-core kernel is enabled once its layouts are validated
         DensePlan p;
         p.compose = false;
         p.n = n;
@@ -47,6 +46,7 @@ ptdr_status make_dense_plan(bool compose, int n, ptdr_dtype in_t, ptdr_dtype out
         p.calc = Calc::F32;
         p.kernel = DenseKernel::Tc14;
         p.single = true;
+        p.ws_bytes = tc14_staged_workspace();
         *plan = p;
         return PTDR_OK;
     }
@@ -64,8 +64,7 @@ ptdr_status make_dense_plan(bool compose, int n, ptdr_dtype in_t, ptdr_dtype out
         p.kernel = DenseKernel::Row14;
         p.single = true;
         // the clustered complex64 kernel exchanges through a scratch in the workspace
-        if (in_t == PTDR_C64 && out_t == PTDR_C64)
-            p.ws_bytes = std::max(dense14_x4_workspace(), dense14_staged_workspace());
+        if (in_t == PTDR_C64 && out_t == PTDR_C64) p.ws_bytes = dense14_staged_workspace();
         *plan = p;
         return PTDR_OK;
     }
@@ -106,14 +105,14 @@ ptdr_status execute_dense(const DensePlan& p, const void* in, void* out, void* w
     const uint64_t N = 1ull << p.n;
     cudaError_t e = cudaSuccess;
     if (p.kernel == DenseKernel::Tc14) {
-        if (!tc14_supported(in, p.in_t, p.out_t)) return PTDR_ERR_INVALID_ARG; // needs 16-byte alignment
-        e = launch_tc14(in, out, st, s);
+        if ((uintptr_t)in % 16 || (uintptr_t)out % 16) return PTDR_ERR_INVALID_ARG; // 16-byte copies
+        e = launch_tc14_staged(in, out, ws, st, s);
         return e == cudaSuccess ? PTDR_OK : PTDR_ERR_CUDA;
     }
     if (p.kernel == DenseKernel::Row14) {
         // complex64 -> complex64 with a 16-byte aligned input takes the
         // clustered tile kernel; other type pairs the one-mask-per-CTA kernel
-        if (ws && dense14_x4_supported(in, p.in_t, p.out_t))
+        if (ws && p.in_t == PTDR_C64 && p.out_t == PTDR_C64 && (uintptr_t)in % 16 == 0 && (uintptr_t)out % 16 == 0)
             e = launch_dense14_staged(in, out, ws, st, s);
         else
             e = launch_row14(in, p.in_t, out, p.out_t, st, s);

@@ -22,8 +22,9 @@ struct StridedPass {
 
 enum class DenseKernel {
     Tiles,      // generic tile kernels (any n, FP32/FP64)
-    Row14,      // n = 14 FP32 decompose: one CTA per mask, register rounds 5/5/4
-    Tc14,       // n = 14 split-bf16 tensor-core decompose (clusters of 4)
+    Row14,      // n = 14 FP32 decompose: staged two-pass kernel (complex64, 16-byte
+                // aligned), otherwise one CTA per mask with register rounds 5/5/4
+    Tc14,       // n = 14 split-bf16 decompose, tensor-core stage over column blocks
 };
 
 struct DensePlan {
@@ -52,13 +53,10 @@ std::vector<StridedPass> strided_schedule(int b0, int n, size_t elem_bytes);
 
 cudaError_t launch_row14(const void* A, ptdr_dtype a_t, void* C, ptdr_dtype c_t,
                          unsigned int* status, cudaStream_t s);
-bool dense14_x4_supported(const void* A, ptdr_dtype a_t, ptdr_dtype c_t);
-bool tc14_supported(const void* A, ptdr_dtype a_t, ptdr_dtype c_t);
-cudaError_t launch_tc14(const void* A, void* C, unsigned int* status, cudaStream_t s);
-cudaError_t launch_dense14_x4(const void* A, void* C, void* ws, unsigned int* status, cudaStream_t s);
-size_t dense14_x4_workspace();
 cudaError_t launch_dense14_staged(const void* A, void* C, void* ws, unsigned int* status, cudaStream_t s);
 size_t dense14_staged_workspace();
+cudaError_t launch_tc14_staged(const void* A, void* C, void* ws, unsigned int* status, cudaStream_t s);
+size_t tc14_staged_workspace();
 
 // shared helpers (ptdr_api.cu)
 ptdr_status device_ready(int* dev);

@@ -79,6 +79,23 @@ def test_config_dense_n14(a14, ref14, prec):
     assert ptdr.last_device_status() == 0
 
 
+def test_config_dense_n14_split_bf16_tc(a14, ref14):
+    """dense n=14 complex64 on the split-bf16 tensor-core path: error vs the FP64 oracle <= 2e-6."""
+    C = host(ptdr.decompose(dev(a14), precision="bf16x3"))
+    err = rel_err(C, ref14)
+    print(f"split-bf16 TC n=14 rel err {err:.3e}")
+    assert err <= TOL["bf16x3"]
+    xs = workloads.sample_masks(14, 14, count=6)
+    assert rel_err(C[xs.astype(np.int64)], oracle.direct(a14, xs=xs)) <= TOL["bf16x3"]
+    assert ptdr.last_device_status() == 0
+
+
+def test_split_tc_unsupported_sizes():
+    A = dev(workloads.dense(6, 1, dtype=np.complex64))
+    with pytest.raises(ptdr.PtdrError):
+        ptdr.decompose(A, precision="bf16x3")
+
+
 def test_n14_fp64_into_c64_workspace_path(a14, ref14):
     C = host(ptdr.decompose(dev(a14), precision="fp64", out_dtype=torch.complex64))
     assert rel_err(C, ref14) <= 1e-6  # rounded to complex64 once at the end

@@ -105,18 +105,6 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
            (1ull << 46);
 }
 
-__device__ __forceinline__ void split3(float x, uint16_t& hi, uint16_t& mid, uint16_t& lo)
-{
-    const __nv_bfloat16 h = __float2bfloat16_rn(x);
-    const float r1 = x - __bfloat162float(h);
-    const __nv_bfloat16 m = __float2bfloat16_rn(r1);
-    const float r2 = r1 - __bfloat162float(m);
-    const __nv_bfloat16 l = __float2bfloat16_rn(r2);
-    hi = __bfloat16_as_ushort(h);
-    mid = __bfloat16_as_ushort(m);
-    lo = __bfloat16_as_ushort(l);
-}
-
 __device__ __forceinline__ uint32_t pack2(uint16_t a, uint16_t b) { return (uint32_t)a | ((uint32_t)b << 16); }
 
 #define TC_LD64(r, addr)                                                                              \
@@ -259,47 +247,65 @@ __global__ void __launch_bounds__(kThreads, 1)
             const float2* srow = tab.stage + ((size_t)(xt % kSlots) * kT + xl) * kN;
             // B[cb][n = 2 zl + ri]: lane (cb & 7, zq & 3) takes 4 complex (32 bytes),
             // so a warp reads 8 rows x 128 bytes and writes 32 distinct 16-byte
-            // slots of 4 core matrices per split.
-#pragma unroll 2
+            // slots of 4 core matrices per split.  All 16 loads are issued first;
+            // each split is stored and handed to the tensor core as soon as it is
+            // complete, so the next split's stores overlap the previous MMAs.
+            float4 a[16];
+#pragma unroll
             for (int i = 0; i < 8; ++i) {
                 const int task = t + kThreads * i; // 4096 tasks = 128 cb x 32 zq
-                const int cbl = task & 7, zql = (task >> 3) & 3, rest = task >> 5;
-                const int zq = zql + 4 * (rest & 7); // 0..31
-                const int cbv = cbl + 8 * (rest >> 3); // 0..127
+                const int rest = task >> 5;
+                const int zq = ((task >> 3) & 3) + 4 * (rest & 7);
+                const int cbv = (task & 7) + 8 * (rest >> 3);
                 const float4* p = reinterpret_cast<const float4*>(srow + (size_t)cbv * kT + 4 * zq);
-                const float4 a0 = __ldcg(p), a1 = __ldcg(p + 1);
-                const float f[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-                uint16_t hi[8], mi[8], lo[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) split3(f[u], hi[u], mi[u], lo[u]);
-                const uint32_t off = (uint32_t)((cbv >> 3) * 32 + zq) * 128u + (uint32_t)(cbv & 7) * 16u;
-                *reinterpret_cast<uint4*>(opp + off) =
-                    make_uint4(pack2(hi[0], hi[1]), pack2(hi[2], hi[3]), pack2(hi[4], hi[5]), pack2(hi[6], hi[7]));
-                *reinterpret_cast<uint4*>(opp + 65536u + off) =
-                    make_uint4(pack2(mi[0], mi[1]), pack2(mi[2], mi[3]), pack2(mi[4], mi[5]), pack2(mi[6], mi[7]));
-                *reinterpret_cast<uint4*>(opp + 131072u + off) =
-                    make_uint4(pack2(lo[0], lo[1]), pack2(lo[2], lo[3]), pack2(lo[4], lo[5]), pack2(lo[6], lo[7]));
+                a[2 * i] = __ldcg(p);
+                a[2 * i + 1] = __ldcg(p + 1);
             }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncthreads();
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            if (t == 0) {
 #pragma unroll 1
-                for (int s = 0; s < 3; ++s)
+            for (int sp = 0; sp < 3; ++sp) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int task = t + kThreads * i;
+                    const int rest = task >> 5;
+                    const int zq = ((task >> 3) & 3) + 4 * (rest & 7);
+                    const int cbv = (task & 7) + 8 * (rest >> 3);
+                    float f[8] = {a[2 * i].x, a[2 * i].y, a[2 * i].z, a[2 * i].w,
+                                  a[2 * i + 1].x, a[2 * i + 1].y, a[2 * i + 1].z, a[2 * i + 1].w};
+                    uint16_t q[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        // peel split sp off the remainder: q = bf16(f), f -= q
+                        const __nv_bfloat16 b = __float2bfloat16_rn(f[u]);
+                        q[u] = __bfloat16_as_ushort(b);
+                        f[u] -= __bfloat162float(b);
+                    }
+                    a[2 * i] = make_float4(f[0], f[1], f[2], f[3]);
+                    a[2 * i + 1] = make_float4(f[4], f[5], f[6], f[7]);
+                    const uint32_t off = (uint32_t)((cbv >> 3) * 32 + zq) * 128u + (uint32_t)(cbv & 7) * 16u;
+                    *reinterpret_cast<uint4*>(opp + (uint32_t)sp * 65536u + off) =
+                        make_uint4(pack2(q[0], q[1]), pack2(q[2], q[3]), pack2(q[4], q[5]), pack2(q[6], q[7]));
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncthreads();
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                if (t == 0) {
 #pragma unroll 1
                     for (int kk = 0; kk < 8; ++kk) {
                         const uint64_t da = sdesc(h_a + (uint32_t)kk * 256u, 128u, 2048u);
-                        const uint64_t db = sdesc(op_a + (uint32_t)s * 65536u + (uint32_t)kk * 8192u, 4096u, 128u);
-                        const uint32_t acc = (s | kk) ? 1u : 0u;
+                        const uint64_t db = sdesc(op_a + (uint32_t)sp * 65536u + (uint32_t)kk * 8192u, 4096u, 128u);
+                        const uint32_t acc = (sp | kk) ? 1u : 0u;
                         asm volatile(
                             "{ .reg .pred p; setp.ne.u32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(
                                 tmem),
                             "l"(da), "l"(db), "r"(idesc), "r"(acc)
                             : "memory");
                     }
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar_a)
-                             : "memory");
+                    if (sp == 2)
+                        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                         bar_a)
+                                     : "memory");
+                }
             }
             // the staging row is in shared memory now: drop its L2 lines
 #pragma unroll

@@ -30,6 +30,35 @@ N_QUBITS = 14
 SEED = 14
 METRIC = "Pauli coeffs/s and HBM GB/s at n=14, split-BF16 TC vs FP64 plain"
 
+# DRAM bytes (read + write) per launch of the dominant kernel of each n = 14
+# path, from one ncu capture each (summaries under profiles/).  A figure is
+# reported only while the sources it was taken from are unchanged.
+NCU_TRAFFIC = {
+    "bf16x3": {"kernel": "k_tc14_staged", "bytes": 2_240_427_000 + 2_394_227_000,
+               "sources": {"paper_2403_11644_gb300/csrc/k_tc14s.cu":
+                           "cbdc3fff7affaf4bc3c668234a11d5a59ceaf03661cefb0bb704da122d899c29",
+                           "paper_2403_11644_gb300/csrc/common.cuh":
+                           "f41af31f86534a7bc1c1c9a73b10f6d27e738589ae7e9bb8fe5f42eb0a9e6cc1"}},
+    "fp32": {"kernel": "k_dense14_staged", "bytes": 2_157_797_000 + 2_158_074_000,
+             "sources": {"paper_2403_11644_gb300/csrc/k_dense14s.cu":
+                         "0ca9f8674df9a8b43490c448728f48d96a7bc33a9cbd206e4409619055ad01be",
+                         "paper_2403_11644_gb300/csrc/common.cuh":
+                         "f41af31f86534a7bc1c1c9a73b10f6d27e738589ae7e9bb8fe5f42eb0a9e6cc1"}},
+}
+
+
+def ncu_traffic(prec, n):
+    """(kernel, bytes per launch) from the capture table, bytes None if stale."""
+    import hashlib
+    e = NCU_TRAFFIC.get(prec)
+    if e is None or n != 14:
+        return None, None
+    for rel, sha in e["sources"].items():
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != sha:
+                return e["kernel"], None
+    return e["kernel"], e["bytes"]
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -238,6 +267,7 @@ def main():
     # our kernels per step: the n = 14 complex64 paths are one persistent launch
     # (plus a 4 KiB memset of the work-queue counters)
     launches_per_step = 1 if (N_QUBITS == 14 and prec in ("fp32", "bf16x3")) else None
+    kernel_name, traffic = ncu_traffic(prec, N_QUBITS)
 
     result = None
     if rank == 0:
@@ -254,7 +284,8 @@ def main():
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved / hbm_peak, "peak_source": peak_kind,
-                         "traffic": None, "algorithmic_bytes_per_launch": alg_bytes,
+                         "traffic": traffic, "kernel": kernel_name,
+                         "algorithmic_bytes_per_launch": alg_bytes,
                          "kernel_ms": kern_ms},
             "clocks": clk.summary(),
             "gpu_launches": None if launches_per_step is None else launches_per_step * args.steps,

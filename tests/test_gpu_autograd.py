@@ -1,4 +1,4 @@
-"""Autograd of loss = sum_P w_P |c_P|^2 through ptdr (config 4b)."""
+"""Autograd of loss = sum_P w_P |c_P|^2 through ptdr (n = 5 and n = 10)."""
 import numpy as np
 import pytest
 import torch

@@ -1,4 +1,4 @@
-"""GPU parity of the persistent batched launch (config 4a)."""
+"""GPU parity of the persistent batched launch (512 matrices of uneven size)."""
 import numpy as np
 import pytest
 import torch
@@ -27,7 +27,7 @@ def test_uneven_small_batch_fp64():
     assert ptdr.last_device_status() == 0
 
 
-def test_config_batched_512():
+def test_workload_batched_512():
     """512 seeded complex64 matrices, n ~ U{4..11}, one persistent launch."""
     ns, mats = workloads.batched(seed=4)
     outs = ptdr.decompose_batched([dev(m) for m in mats], precision="fp32")

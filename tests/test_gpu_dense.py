@@ -1,4 +1,4 @@
-"""GPU parity of dense decompose/compose against the CPU oracle (configs 1, 2, 5)."""
+"""GPU parity of dense decompose/compose against the CPU oracle (n = 1..15, the n = 6, 12 and 14 workloads)."""
 import numpy as np
 import pytest
 import torch
@@ -33,7 +33,7 @@ def test_all_sizes(n, prec, adt):
 
 
 @pytest.mark.parametrize("hermitian", [False, True])
-def test_config_dense_n6(hermitian):
+def test_workload_dense_n6(hermitian):
     """dense n=6 complex128, general and Hermitian, FP64 against every oracle route."""
     A = workloads.dense(6, 106 if hermitian else 6, hermitian=hermitian)
     C = host(ptdr.decompose(dev(A), precision="fp64"))
@@ -46,7 +46,7 @@ def test_config_dense_n6(hermitian):
 @pytest.mark.parametrize("hermitian", [False, True])
 @pytest.mark.parametrize("prec,adt", [("fp64", np.complex128), ("fp32", np.complex64),
                                       ("fp64", np.complex64)])
-def test_config_dense_n12(hermitian, prec, adt):
+def test_workload_dense_n12(hermitian, prec, adt):
     """dense n=12, complex128/complex64, general/Hermitian, FP64 and FP32 paths."""
     A = workloads.dense(12, 112 if hermitian else 12, dtype=adt, hermitian=hermitian)
     C = host(ptdr.decompose(dev(A), precision=prec))
@@ -68,7 +68,7 @@ def ref14(a14):
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
-def test_config_dense_n14(a14, ref14, prec):
+def test_workload_dense_n14(a14, ref14, prec):
     """dense n=14 complex64: full output against the FWHT check, sampled rows against the direct trace."""
     Ad = dev(a14)
     out_dtype = torch.complex128 if prec == "fp64" else torch.complex64
@@ -79,7 +79,7 @@ def test_config_dense_n14(a14, ref14, prec):
     assert ptdr.last_device_status() == 0
 
 
-def test_config_dense_n14_split_bf16_tc(a14, ref14):
+def test_workload_dense_n14_split_bf16_tc(a14, ref14):
     """dense n=14 complex64 on the split-bf16 tensor-core path: error vs the FP64 oracle <= 2e-6."""
     C = host(ptdr.decompose(dev(a14), precision="bf16x3"))
     err = rel_err(C, ref14)

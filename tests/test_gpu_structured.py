@@ -1,4 +1,4 @@
-"""GPU parity of the band-diagonal path (config 3 and general bands)."""
+"""GPU parity of the band-diagonal path (tridiagonal n = 22, diagonal n = 26 and general bands)."""
 import numpy as np
 import pytest
 import torch
@@ -59,7 +59,7 @@ def test_real_symmetric_tridiagonal_real_output(n):
         assert rel_err(C, dense[masks.astype(np.int64)].real) <= TOL["fp64"]
 
 
-def test_config_tridiagonal_n22():
+def test_workload_tridiagonal_n22():
     """real symmetric tridiagonal n=22 stored as 3 bands, FP64, only the n+1 masks."""
     n = 22
     bands = workloads.tridiagonal(n, 22)
@@ -71,7 +71,7 @@ def test_config_tridiagonal_n22():
     assert ptdr.last_device_status() == 0
 
 
-def test_config_diagonal_n26():
+def test_workload_diagonal_n26():
     """real diagonal n=26 (U(-1,1)), FP64: only mask 0."""
     n = 26
     d = workloads.diagonal(n, 26)

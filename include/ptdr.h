@@ -94,8 +94,10 @@ typedef enum {
  *   C, c_type   device, 4^n elements of c_type in {C64, C128}; C[x*2^n + z].
  *   n           1 <= n <= 15.
  *   prec        FP64: any a_type/c_type.  FP32: any a_type/c_type (C128 input
- *               is rounded to float32 on load).  SPLIT_*_TC: a_type = c_type
- *               = C64.
+ *               is rounded to float32 on load).  SPLIT_BF16_TC: n = 14,
+ *               a_type = c_type = C64, with A, C and the workspace 32-byte
+ *               aligned (PTDR_ERR_INVALID_ARG otherwise); other n or types
+ *               return PTDR_ERR_UNSUPPORTED.  SPLIT_FP16_TC: unsupported.
  *   workspace   device scratch of at least ptdr_workspace_size() bytes (may
  *               be NULL when that size is 0).
  * Returns PTDR_OK once the work is enqueued on `stream`.

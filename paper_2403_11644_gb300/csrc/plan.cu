@@ -46,7 +46,7 @@ ptdr_status make_dense_plan(bool compose, int n, ptdr_dtype in_t, ptdr_dtype out
         p.calc = Calc::F32;
         p.kernel = DenseKernel::Tc14;
         p.single = true;
-        p.ws_bytes = tc14_staged_workspace();
+        p.ws_bytes = tc14_pipe_workspace();
         *plan = p;
         return PTDR_OK;
     }
@@ -105,8 +105,9 @@ ptdr_status execute_dense(const DensePlan& p, const void* in, void* out, void* w
     const uint64_t N = 1ull << p.n;
     cudaError_t e = cudaSuccess;
     if (p.kernel == DenseKernel::Tc14) {
-        if ((uintptr_t)in % 16 || (uintptr_t)out % 16) return PTDR_ERR_INVALID_ARG; // 16-byte copies
-        e = launch_tc14_staged(in, out, ws, st, s);
+        // 32-byte vector loads and stores of A, C and the staging rows
+        if ((uintptr_t)in % 32 || (uintptr_t)out % 32 || (uintptr_t)ws % 32) return PTDR_ERR_INVALID_ARG;
+        e = launch_tc14_pipe(in, out, ws, st, s);
         return e == cudaSuccess ? PTDR_OK : PTDR_ERR_CUDA;
     }
     if (p.kernel == DenseKernel::Row14) {

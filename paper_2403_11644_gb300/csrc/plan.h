@@ -55,8 +55,8 @@ cudaError_t launch_row14(const void* A, ptdr_dtype a_t, void* C, ptdr_dtype c_t,
                          unsigned int* status, cudaStream_t s);
 cudaError_t launch_dense14_staged(const void* A, void* C, void* ws, unsigned int* status, cudaStream_t s);
 size_t dense14_staged_workspace();
-cudaError_t launch_tc14_staged(const void* A, void* C, void* ws, unsigned int* status, cudaStream_t s);
-size_t tc14_staged_workspace();
+cudaError_t launch_tc14_pipe(const void* A, void* C, void* ws, unsigned int* status, cudaStream_t s);
+size_t tc14_pipe_workspace();
 
 // shared helpers (ptdr_api.cu)
 ptdr_status device_ready(int* dev);

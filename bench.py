@@ -58,6 +58,137 @@ def ncu_traffic(prec, n):
     return e["kernel"], e["bytes"]
 
 
+# FP64 add throughput of one GB300 (adds/s), measured with an add-chain
+# microbenchmark: the bound of the FP64 transforms.
+FP64_ADDS_PER_S = 0.505e12
+
+
+def _timed(fn, stream, reps=3, flush=None):
+    """Mean CUDA-event time (ms) of fn() over reps, after one warm-up call."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    tot = 0.0
+    for _ in range(reps):
+        if flush is not None:
+            flush()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        tot += a.elapsed_time(b)
+    return tot / reps
+
+
+def measure_rows(dev, stream, hbm_peak):
+    """Throughput of the other hot-path rows on their workloads (rank 0, N = 1).
+
+    The band inputs are the seeded workloads of the GPU tests; the dense and
+    batched inputs are seeded draws made on the device (timing only; their
+    parity is covered by the GPU tests).  Each entry reports its own bound:
+    HBM bytes against the measured copy bandwidth, or FP64 adds against the
+    FP64 add rate.
+    """
+    import torch
+    import paper_2403_11644_gb300 as ptdr
+    g = torch.Generator(device=dev)
+    rows = {}
+    flush_buf = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    def flush():
+        flush_buf.fill_(1)
+
+    def hbm(ms, nbytes):
+        gbs = nbytes / ms / 1e6
+        return {"bound": "hbm", "achieved_gbs": gbs, "frac": gbs / hbm_peak}
+
+    def fp64(ms, adds):
+        r = adds / (ms * 1e-3)
+        return {"bound": "fp64_alu", "achieved_adds_per_s": r, "frac": r / FP64_ADDS_PER_S}
+
+    def entry(name, fn, work):
+        try:
+            rows[name] = fn()
+            rows[name].update(work(rows[name]["ms"]))
+        except Exception as e:  # report, never hide
+            rows[name] = {"error": str(e)}
+
+    # a6: diagonal n = 26 (mask 0 only) and tridiagonal n = 22 (23 masks), FP64
+    def diag():
+        import workloads
+        bands = torch.from_numpy(workloads.diagonal(26, 26)).reshape(1, -1).to(dev)
+        out = torch.empty((1, 1 << 26), dtype=torch.float64, device=dev)
+        ms = _timed(lambda: ptdr.decompose_structured(bands, 0, out=out), stream)
+        return {"workload": "diagonal n=26 float64", "ms": ms, "coeffs_per_s": (1 << 26) / (ms * 1e-3),
+                "algorithmic_bytes": 2 * 8 << 26}
+    entry("diagonal_n26_fp64", diag, lambda ms: fp64(ms, 26 * (1 << 26)))
+
+    def tri():
+        import workloads
+        bands = torch.from_numpy(workloads.tridiagonal(22, 22)).to(dev)
+        nm = len(ptdr.structured_masks(22, 1))
+        out = torch.empty((nm, 1 << 22), dtype=torch.float64, device=dev)
+        ms = _timed(lambda: ptdr.decompose_structured(bands, 1, out=out), stream)
+        nbytes = 3 * 8 << 22
+        nbytes += nm * 8 << 22
+        return {"workload": "tridiagonal n=22 float64", "ms": ms, "coeffs_per_s": nm * (1 << 22) / (ms * 1e-3),
+                "algorithmic_bytes": nbytes}
+    entry("tridiagonal_n22_fp64", tri, lambda ms: hbm(ms, rows["tridiagonal_n22_fp64"]["algorithmic_bytes"]))
+
+    # a7: 512 matrices of uneven size in one persistent launch, FP32
+    def batched():
+        import workloads
+        ns = workloads.batched_ns(4)
+        g.manual_seed(4)
+        As = [torch.randn((1 << int(n), 1 << int(n)), generator=g, device=dev, dtype=torch.complex64) for n in ns]
+        Cs = [torch.empty_like(a) for a in As]
+        plan = ptdr.BatchedPlan(As, Cs, "fp32")
+        coeffs = int(sum(4 ** int(n) for n in ns))
+        ms = _timed(plan.run, stream, flush=flush)
+        return {"workload": "512 matrices, n ~ U{4..11}, complex64 (seed 4)", "ms": ms,
+                "coeffs_per_s": coeffs / (ms * 1e-3), "algorithmic_bytes": 16 * coeffs}
+    entry("batched_512_fp32", batched, lambda ms: hbm(ms, rows["batched_512_fp32"]["algorithmic_bytes"]))
+
+    # a8: compose (inverse map) n = 14, FP32
+    def comp():
+        g.manual_seed(114)
+        Cc = torch.randn((1 << 14, 1 << 14), generator=g, device=dev, dtype=torch.complex64)
+        Ao = torch.empty_like(Cc)
+        ms = _timed(lambda: ptdr.compose(Cc, out=Ao), stream)
+        return {"workload": "compose n=14 complex64", "ms": ms, "coeffs_per_s": (1 << 28) / (ms * 1e-3),
+                "algorithmic_bytes": 16 << 28}
+    entry("compose_n14_fp32", comp, lambda ms: hbm(ms, 16 << 28))
+
+    # a4: n = 15 (rows too long for one tile: strided HBM passes), FP32
+    def n15():
+        g.manual_seed(15)
+        A15 = torch.randn((1 << 15, 1 << 15), generator=g, device=dev, dtype=torch.complex64)
+        C15 = torch.empty_like(A15)
+        ms = _timed(lambda: ptdr.decompose(A15, precision="fp32", out=C15), stream, reps=2)
+        return {"workload": "dense n=15 complex64", "ms": ms, "coeffs_per_s": (1 << 30) / (ms * 1e-3),
+                "algorithmic_bytes": 16 << 30}
+    entry("dense_n15_fp32", n15, lambda ms: hbm(ms, 16 << 30))
+
+    # dense n = 12 (L2 flushed between repetitions)
+    def n12(prec, odt):
+        def f():
+            g.manual_seed(12)
+            A12 = torch.randn((1 << 12, 1 << 12), generator=g, device=dev, dtype=torch.complex128)
+            C12 = torch.empty_like(A12, dtype=odt)
+            ms = _timed(lambda: ptdr.decompose(A12, precision=prec, out=C12), stream, flush=flush)
+            return {"workload": f"dense n=12 complex128 -> {str(odt).split('.')[-1]} {prec}", "ms": ms,
+                    "coeffs_per_s": (1 << 24) / (ms * 1e-3),
+                    "algorithmic_bytes": (16 + C12.element_size()) << 24}
+        return f
+    entry("dense_n12_fp64", n12("fp64", torch.complex128), lambda ms: fp64(ms, 2 * 12 * (1 << 24)))
+    entry("dense_n12_fp32", n12("fp32", torch.complex64),
+          lambda ms: hbm(ms, rows["dense_n12_fp32"]["algorithmic_bytes"]))
+    del flush_buf
+    torch.cuda.empty_cache()
+    return rows
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -344,6 +475,7 @@ def main():
             except Exception as e:  # report, never hide
                 extra[p2] = {"error": str(e)}
         result["paths"] = extra
+        result["rows"] = measure_rows(dev, stream, hbm_peak)
 
     if rank == 0 and world == 1 and N_QUBITS == 14 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline()

@@ -25,26 +25,34 @@
 // x - hi - mid, which has at most 8 significant bits), so the only rounding
 // of the tensor-core stage is the float32 accumulation; H is exact in bf16.
 //
-// One persistent CTA per SM, warp-specialised:
-//   warps 0-7   loaders: 32-byte loads of 8 rows x 128 bytes per warp
-//               instruction (tile rows from HBM, staging rows from L2), the
-//               XOR permutation (tile jobs), the split, and 16-byte stores
-//               into MN-major core matrices of a 4-deep ring of K chunks
-//               (32 rows of K each);
-//   warp 12     one lane issues 6 MMAs per chunk and commits each chunk back
-//               to the ring and each job to one of two tensor-memory
+// One persistent CTA per SM, warp-specialised, every hand-off an mbarrier:
+//   warp 17     producer: takes jobs from the queue and copies each K chunk
+//               (32 rows of 1 KiB: tile rows from HBM, staging rows from L2)
+//               with bulk asynchronous copies into a 3-deep ring of padded
+//               raw buffers (row pitch 1040 bytes);
+//   warps 0-7   loaders: raw float32 rows from shared memory, the XOR
+//               permutation (tile jobs), the split, and 16-byte stores into
+//               the MN-major core matrices of a 2-deep operand ring;
+//   warp 16     one lane issues the MMAs of each chunk and commits the chunk
+//               back to the ring and each job to one of two tensor-memory
 //               accumulators (2 x 256 columns);
-//   warps 8-11  epilogue: tcgen05.ld of the accumulator, sign or phase and
-//               scale, coalesced stores (staging rows, or 32-byte pieces of
-//               C rows).
-// So the loads of one job, the MMAs of the previous one and the epilogue of
-// the one before overlap on each SM.
+//   warps 8-15  epilogue: tcgen05.ld of the accumulator, sign or phase and
+//               scale, coalesced stores.
+// Tile jobs compute D = H * U (M = zl, N = (xl, re/im)): a warp's lanes are
+// consecutive zl, so each staging store covers 256 contiguous bytes.  Row
+// jobs compute the transposed product D^T = B^T * H (M = (zl, re/im) in two
+// halves of 128, N = zb) so that a warp's lanes are 16 consecutive complex
+// outputs: one 128-byte line of C per store; the (-i)^{|x&z|} re/im swap
+// takes the partner lane's value by shuffle.
+// So the copies of one job, the split of the next chunk, the MMAs and the
+// epilogue of the job before overlap on each SM.
 //
 // Jobs come from one atomic queue in x-tile-major rounds: round r holds the
 // 128 tile jobs of x-tile r, then the 128 row jobs of x-tile r-1.  A row job
 // waits (bounded) until its x-tile's tile jobs are done; a tile job waits
 // (bounded) before writing its staging slot until the row jobs of the x-tile
-// that used the slot before are done.  Within a CTA every stage waits only
+// that used the slot before are done (each epilogue warp counts itself, so a
+// finished x-tile pass is 128 jobs x 8 warps).  Within a CTA every stage waits only
 // on older jobs, so the earliest unfinished job can always proceed.  Every
 // wait is bounded: on time-out the kernel records PTDR_ERR_TIMEOUT, each
 // role leaves its loop, in-flight MMAs are awaited (bounded) and the tensor
@@ -65,24 +73,28 @@ constexpr int kN = 1 << kLog;
 constexpr int kT = 128;
 constexpr int kTiles = kN / kT;
 constexpr int kLoadWarps = 8;
-constexpr int kEpiWarps = 4;
-constexpr int kMmaWarp = kLoadWarps + kEpiWarps;
-constexpr int kThreads = (kMmaWarp + 1) * 32; // 416
-constexpr int kLoadThreads = kLoadWarps * 32;
-constexpr int kEpiThreads = kEpiWarps * 32;
+constexpr int kEpiWarps = 8;
+constexpr int kMmaWarp = kLoadWarps + kEpiWarps; // 16
+constexpr int kProdWarp = kMmaWarp + 1;          // 17
+constexpr int kThreads = (kProdWarp + 1) * 32;   // 576
 constexpr int kChunks = 4;                        // K chunks of 32 rows per job
 constexpr uint32_t kSplitBytes = 32u * 256u * 2u; // one split of a chunk: 32 K x 256 N bf16
-constexpr uint32_t kChunkSmem = 3u * kSplitBytes;
-constexpr uint32_t kRingBytes = kChunks * kChunkSmem;
+constexpr uint32_t kChunkSmem = 3u * kSplitBytes; // 48 KiB operand chunk
+constexpr int kOpSlots = 2;
+constexpr int kRawSlots = 3;
+constexpr uint32_t kRawPitch = 1040u;            // 1 KiB row + 16 bytes: conflict-free 8-row reads
+constexpr uint32_t kRawSlotBytes = 32u * kRawPitch;
+constexpr uint32_t kRawOff = kOpSlots * kChunkSmem;
+constexpr uint32_t kHOff = kRawOff + kRawSlots * kRawSlotBytes;
 constexpr uint32_t kHBytes = kT * kT * 2u;
-constexpr uint32_t kSmemBytes = kRingBytes + kHBytes + 1024u; // + alignment slack
-constexpr uint32_t kTmemCols = 512;                           // two 128 x 256 float32 accumulators
-constexpr int kSlots = 4;                                     // staging slots (x-tiles in flight)
+constexpr uint32_t kSmemBytes = kHOff + kHBytes + 128u; // + alignment slack
+constexpr uint32_t kTmemCols = 512;                     // two 128 x 256 float32 accumulators
+constexpr int kSlots = 4;                               // staging slots (x-tiles in flight)
 constexpr int kPerRound = 2 * kT;
 constexpr int kItems = (kTiles + 1) * kPerRound;
+constexpr int kDoneTarget = kT * kEpiWarps; // epilogue warps per finished x-tile pass
 constexpr unsigned long long kWaitNs = 1000000000ull; // bound of every wait: 1 s
 
-enum : int { kBarLoad = 1, kBarEpi = 2 };
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -91,19 +103,6 @@ __device__ __forceinline__ unsigned long long now_ns()
     unsigned long long t;
     asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
     return t;
-}
-
-__device__ __forceinline__ void named_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
-
-// Named barrier that also returns the OR of v over the participating threads.
-__device__ __forceinline__ bool named_sync_or(int id, int n, bool v)
-{
-    uint32_t r;
-    asm volatile("{ .reg .pred p, q; setp.ne.u32 q, %1, 0; bar.red.or.pred p, %2, %3, q; selp.u32 %0, 1, 0, p; }"
-                 : "=r"(r)
-                 : "r"((uint32_t)v), "r"(id), "r"(n)
-                 : "memory");
-    return r != 0;
 }
 
 __device__ __forceinline__ int ld_acquire(const int* p)
@@ -124,12 +123,15 @@ __device__ __forceinline__ bool wait_count(const int* p, int target, const volat
     return true;
 }
 
+// One test of an mbarrier phase; a waiting thread is suspended in hardware
+// (up to 20 us, woken early when the phase completes) so that polling warps
+// do not take issue slots from the working ones.
 __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
 {
     uint32_t done;
-    asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+    asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3; selp.u32 %0, 1, 0, p; }"
                  : "=r"(done)
-                 : "r"(bar), "r"(parity)
+                 : "r"(bar), "r"(parity), "r"(20000u)
                  : "memory");
     return done != 0;
 }
@@ -150,6 +152,38 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar)
     asm volatile("{ .reg .b64 st; mbarrier.arrive.shared::cta.b64 st, [%0]; }" ::"r"(bar) : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("{ .reg .b64 st; mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1; }" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+// Bulk asynchronous copy global -> shared, completion counted on an mbarrier.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void lds128(uint32_t addr, float& a, float& b, float& c, float& d)
+{
+    asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4];" : "=f"(a), "=f"(b), "=f"(c), "=f"(d) : "r"(addr));
+}
+
+// Lane 0 of the warp runs a bounded mbarrier wait; every lane gets the result.
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, const volatile int* abort_flag, int lane,
+                                          unsigned int* st)
+{
+    int ok = 1;
+    if (lane == 0 && !mbar_wait(bar, parity, abort_flag)) {
+        report_status(st, PTDR_ERR_TIMEOUT);
+        *const_cast<volatile int*>(abort_flag) = 1;
+        ok = 0;
+    }
+    return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
 // Shared-memory matrix descriptor without swizzle (version 1).  K-major:
 // lbo = K-direction core-matrix stride, sbo = M/N-direction stride.
 // MN-major: lbo = K-direction stride, sbo = M/N-direction stride.
@@ -157,20 +191,6 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
 {
     return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
            (1ull << 46);
-}
-
-__device__ __forceinline__ void ld8(const float* p, float (&f)[8])
-{
-    asm volatile("ld.global.cg.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=f"(f[0]), "=f"(f[1]), "=f"(f[2]), "=f"(f[3]), "=f"(f[4]), "=f"(f[5]), "=f"(f[6]), "=f"(f[7])
-                 : "l"(p));
-}
-
-__device__ __forceinline__ void st8_cs(float* p, const float (&f)[8])
-{
-    asm volatile("st.global.cs.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "f"(f[0]), "f"(f[1]), "f"(f[2]),
-                 "f"(f[3]), "f"(f[4]), "f"(f[5]), "f"(f[6]), "f"(f[7])
-                 : "memory");
 }
 
 __device__ __forceinline__ void sts128(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d)
@@ -186,18 +206,21 @@ __device__ __forceinline__ uint32_t hi16x2(float a, float b)
 
 __device__ __forceinline__ float trunc_bf16(float a) { return __uint_as_float(__float_as_uint(a) & 0xFFFF0000u); }
 
-// Exact three-way split of 8 floats into bf16 parts, written as three 16-byte
-// core-matrix rows (hi at a, mid at a + kSplitBytes, lo at a + 2 kSplitBytes).
-__device__ __forceinline__ void split_store(const float (&f)[8], uint32_t a)
+// Exact three-way split of 8 floats into bf16 parts, packed as three 16-byte
+// core-matrix rows: w[0..3] = hi, w[4..7] = mid, w[8..11] = lo.
+__device__ __forceinline__ void split3(const float (&f)[8], uint32_t (&w)[12])
 {
     float r[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) r[k] = f[k] - trunc_bf16(f[k]);
-    sts128(a, hi16x2(f[0], f[1]), hi16x2(f[2], f[3]), hi16x2(f[4], f[5]), hi16x2(f[6], f[7]));
-    sts128(a + kSplitBytes, hi16x2(r[0], r[1]), hi16x2(r[2], r[3]), hi16x2(r[4], r[5]), hi16x2(r[6], r[7]));
+#pragma unroll
+    for (int k = 0; k < 4; ++k) w[k] = hi16x2(f[2 * k], f[2 * k + 1]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) w[4 + k] = hi16x2(r[2 * k], r[2 * k + 1]);
 #pragma unroll
     for (int k = 0; k < 8; ++k) r[k] = r[k] - trunc_bf16(r[k]);
-    sts128(a + 2u * kSplitBytes, hi16x2(r[0], r[1]), hi16x2(r[2], r[3]), hi16x2(r[4], r[5]), hi16x2(r[6], r[7]));
+#pragma unroll
+    for (int k = 0; k < 4; ++k) w[8 + k] = hi16x2(r[2 * k], r[2 * k + 1]);
 }
 
 // v <- (v[j ^ p]) for the four complex values j = 0..3 held as 8 floats.
@@ -240,22 +263,21 @@ struct TcPipeTables {
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc14_pipe(const float2* __restrict__ A, float2* __restrict__ C, TcPipeTables tab, unsigned int* st)
 {
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    __shared__ __align__(8) unsigned long long bar_full[kChunks], bar_empty[kChunks], bar_tfull[2], bar_tempty[2],
-        bar_exit;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) unsigned long long raw_full[kRawSlots], raw_empty[kRawSlots], op_full[kOpSlots],
+        op_empty[kOpSlots], t_full[2], t_empty[2], bar_exit;
     __shared__ int s_jobq[8];
-    __shared__ int s_load_job[2];
-    __shared__ int s_epi_job;
     __shared__ volatile int s_abort;
     __shared__ uint32_t s_tmem;
 
     const uint32_t raw_a = su32(smem_raw);
-    const uint32_t ring_a = (raw_a + 1023u) & ~1023u;
-    const uint32_t h_a = ring_a + kRingBytes;
+    const uint32_t base = (raw_a + 127u) & ~127u;
+    const uint32_t op_a = base, rawb_a = base + kRawOff, h_a = base + kHOff;
     uint16_t* hmat = reinterpret_cast<uint16_t*>(smem_raw + (h_a - raw_a));
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
 
-    // H_128 as the K-major A operand: element (zb, cb) = (-1)^{|zb & cb|}
+    // H_128 in K-major core matrices (A operand of tile jobs, B operand of
+    // row jobs; H is symmetric): element (r, k) = (-1)^{|r & k|}
     for (int e = t; e < kT * kT; e += kThreads) {
         const int z = e >> 7, k = e & 127;
         hmat[((z >> 3) * 16 + (k >> 3)) * 64 + (z & 7) * 8 + (k & 7)] = (__popc(z & k) & 1) ? 0xBF80u : 0x3F80u;
@@ -266,13 +288,17 @@ __global__ void __launch_bounds__(kThreads, 1)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (t == 0) {
-        for (int i = 0; i < kChunks; ++i) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&bar_full[i])), "r"(kLoadThreads));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bar_empty[i])));
+        for (int i = 0; i < kRawSlots; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&raw_full[i])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&raw_empty[i])), "r"(kLoadWarps));
+        }
+        for (int i = 0; i < kOpSlots; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&op_full[i])), "r"(kLoadWarps));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&op_empty[i])));
         }
         for (int i = 0; i < 2; ++i) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bar_tfull[i])));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&bar_tempty[i])), "r"(kEpiThreads));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&t_full[i])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&t_empty[i])), "r"(kEpiWarps));
         }
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bar_exit)));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -285,23 +311,18 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t tmem = s_tmem;
     const uint64_t lim = (uint64_t)kN * kN;
 
-    if (warp < kLoadWarps) {
-        // ============================================================ loaders
-        // warp w: k-group g = w >> 1 of each chunk, N groups a = 4 i' + (lane >> 3)
-        // with i' in [4 (w & 1), 4 (w & 1) + 4); row m&7 = lane & 7.  A warp
-        // instruction covers 8 rows x 4 N groups: full 32-byte sectors in
-        // global memory and 4 conflict-free wavefronts in shared memory.
-        const int g = warp >> 1, ib = 4 * (warp & 1), r7 = lane & 7, ag = lane >> 3;
+    if (warp == kProdWarp) {
+        // ============================================================ producer
         int next = 0;
-        if (t == 0) next = atomicAdd(tab.head, 1);
-        uint32_t L = 0;
-        for (uint32_t it = 0;; ++it) {
-            if (t == 0) {
-                s_load_job[it & 1] = next;
+        if (lane == 0) next = atomicAdd(tab.head, 1);
+        uint32_t Q = 0, J = 0;
+        for (;;) {
+            int job = 0;
+            if (lane == 0) {
+                job = next;
                 if (next < kItems) next = atomicAdd(tab.head, 1);
             }
-            named_sync(kBarLoad, kLoadThreads);
-            const int job = s_load_job[it & 1];
+            job = __shfl_sync(0xffffffffu, job, 0);
             bool tile = false;
             int xt = 0, cb = 0, xl = 0;
             if (job < kItems) {
@@ -317,187 +338,269 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (xt < 0) continue; // empty slot of the first round
                 }
             }
-            bool fail = false;
-            if (t == 0) {
-                if (job < kItems && !tile && !wait_count(tab.done1 + xt, kT, &s_abort)) {
-                    report_status(st, PTDR_ERR_TIMEOUT);
-                    s_abort = 1;
-                    fail = true;
-                }
-                s_jobq[L & 7] = (job < kItems && !fail) ? job : -1;
+            int ok = 1;
+            if (lane == 0 && job < kItems && !tile && !wait_count(tab.done1 + xt, kDoneTarget, &s_abort)) {
+                report_status(st, PTDR_ERR_TIMEOUT);
+                s_abort = 1;
+                ok = 0;
             }
-            fail = named_sync_or(kBarLoad, kLoadThreads, fail);
-            const bool stop = job >= kItems || fail;
-
-            // row sources: tile rows of A, or the staging row of mask x
-            const float* src0;
-            if (tile)
-                src0 = reinterpret_cast<const float*>(A + ((uint64_t)(kT * (cb ^ xt)) << kLog) + (uint64_t)(kT * cb));
-            else
-                src0 = reinterpret_cast<const float*>(tab.stage + ((size_t)(xt % kSlots) * kT + xl) * kN);
-
-            float f[2][4][8];
-            auto issue = [&](int c, float (&buf)[4][8]) {
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int m = 32 * c + 8 * g + r7;
-                    const int a = 4 * (ib + i) + ag;
-                    const int as = tile ? (a ^ (m >> 2)) : a;
-                    const uint64_t off = ((uint64_t)m << (tile ? kLog : 7)) + 4u * (uint32_t)as; // complex units
-                    const bool okb =
-                        !tile || in_bounds(st, ((uint64_t)(kT * (cb ^ xt) + m) << kLog) + (uint64_t)(kT * cb + 4 * as + 3), lim);
-                    if (okb) {
-                        ld8(src0 + 2 * off, buf[i]);
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (job >= kItems || !ok) {
+                // end marker: travels with the next raw chunk
+                if (lane == 0) {
+                    s_jobq[J & 7] = -1;
+                    const uint32_t sl = Q % kRawSlots;
+                    if (Q < (uint32_t)kRawSlots ||
+                        mbar_wait(su32(&raw_empty[sl]), (Q / kRawSlots - 1) & 1, &s_abort))
+                        mbar_arrive(su32(&raw_full[sl]));
+                }
+                break;
+            }
+            if (!tile) {
+                // the staging rows were written through the generic proxy by other
+                // CTAs: acquire their counter, then order the bulk copies after it
+                (void)ld_acquire(tab.done1 + xt);
+                asm volatile("fence.proxy.async;" ::: "memory");
+            }
+            if (lane == 0) s_jobq[J & 7] = job;
+            const char* src0 =
+                tile ? reinterpret_cast<const char*>(A + ((uint64_t)(kT * (cb ^ xt)) << kLog) + (uint64_t)(kT * cb))
+                     : reinterpret_cast<const char*>(tab.stage + ((size_t)(xt % kSlots) * kT + xl) * kN);
+            const uint64_t pitch = tile ? ((uint64_t)kN * 8u) : (uint64_t)kT * 8u; // bytes between K rows
+            bool quit = false;
+            for (int c = 0; c < kChunks; ++c, ++Q) {
+                const uint32_t sl = Q % kRawSlots;
+                int go = 1;
+                if (lane == 0) {
+                    if (Q >= (uint32_t)kRawSlots &&
+                        !mbar_wait(su32(&raw_empty[sl]), (Q / kRawSlots - 1) & 1, &s_abort)) {
+                        report_status(st, PTDR_ERR_TIMEOUT);
+                        s_abort = 1;
+                        go = 0;
                     } else {
-#pragma unroll
-                        for (int k = 0; k < 8; ++k) buf[i][k] = 0.f;
+                        mbar_arrive_tx(su32(&raw_full[sl]), 32u * 1024u);
                     }
                 }
-            };
-            if (!stop) {
-                issue(0, f[0]);
-                issue(1, f[1]);
-            }
-            bool broke = false;
-#pragma unroll
-            for (int c = 0; c < kChunks; ++c) {
-                // the ring slot of chunk c was last read by the previous job's MMAs
-                bool wfail = false;
-                if (t == 0 && L > 0 && !mbar_wait(su32(&bar_empty[c]), (L - 1) & 1, &s_abort)) {
-                    report_status(st, PTDR_ERR_TIMEOUT);
-                    s_abort = 1;
-                    wfail = true;
+                if (!__shfl_sync(0xffffffffu, go, 0)) {
+                    quit = true;
+                    break;
                 }
-                if (named_sync_or(kBarLoad, kLoadThreads, wfail)) {
-                    broke = true;
+                const int row = 32 * c + lane; // K row of the job
+                const bool okb =
+                    !tile || in_bounds(st, ((uint64_t)(kT * (cb ^ xt) + row) << kLog) + (uint64_t)(kT * cb + kT - 1), lim);
+                const char* src = src0 + (okb ? (uint64_t)row * pitch : 0);
+                bulk_g2s(rawb_a + sl * kRawSlotBytes + (uint32_t)lane * kRawPitch, src, 1024u, su32(&raw_full[sl]));
+            }
+            if (quit) break;
+            ++J;
+        }
+    } else if (warp < kLoadWarps) {
+        // ============================================================ loaders
+        // warp w: rows 8 g + (lane & 7) of each chunk, g = w >> 1, and N groups
+        // a = 4 (ib + i) + (lane >> 3), ib = 4 (w & 1).  A warp instruction
+        // covers 8 rows x 4 N groups: 4 conflict-free wavefronts for the raw
+        // reads (pitch 1040) and for the operand stores.
+        const int g = warp >> 1, ib = 4 * (warp & 1), r7 = lane & 7, ag = lane >> 3;
+        uint32_t Q = 0;
+        for (uint32_t J = 0;; ++J) {
+            int job = -1;
+            bool quit = false;
+            for (int c = 0; c < kChunks; ++c, ++Q) {
+                const uint32_t rs = Q % kRawSlots, os = Q % kOpSlots;
+                if (!warp_wait(su32(&raw_full[rs]), (Q / kRawSlots) & 1, &s_abort, lane, st)) {
+                    quit = true;
+                    break;
+                }
+                if (c == 0) job = s_jobq[J & 7];
+                const bool stop = job < 0;
+                bool tile = false;
+                int xt = 0, xl = 0;
+                if (!stop) {
+                    const int r = job / kPerRound, j = job % kPerRound;
+                    tile = j < kT;
+                    xt = tile ? r : r - 1;
+                    xl = j - kT;
+                }
+                // raw rows -> registers
+                float f[4][8];
+                const uint32_t rrow = rawb_a + rs * kRawSlotBytes + (uint32_t)(8 * g + r7) * kRawPitch;
+                const int m = 32 * c + 8 * g + r7;
+                if (!stop) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int a = 4 * (ib + i) + ag;
+                        const int as = tile ? (a ^ (m >> 2)) : a;
+                        lds128(rrow + (uint32_t)as * 32u, f[i][0], f[i][1], f[i][2], f[i][3]);
+                        lds128(rrow + (uint32_t)as * 32u + 16u, f[i][4], f[i][5], f[i][6], f[i][7]);
+                    }
+                }
+                // permute and split in registers; the raw slot is free after this
+                uint32_t w[4][12];
+                if (!stop) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        if (tile) xor_permute(f[i], r7 & 3);
+                        split3(f[i], w[i]);
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(su32(&raw_empty[rs]));
+                // the operand slot was last read by the MMAs of chunk Q - 2
+                if (Q >= (uint32_t)kOpSlots &&
+                    !warp_wait(su32(&op_empty[os]), (Q / kOpSlots - 1) & 1, &s_abort, lane, st)) {
+                    quit = true;
                     break;
                 }
                 if (!stop) {
-                    const uint32_t slot = ring_a + (uint32_t)c * kChunkSmem;
+                    const uint32_t slot = op_a + os * kChunkSmem;
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
-                        const int m = 32 * c + 8 * g + r7;
                         const int a = 4 * (ib + i) + ag;
-                        if (tile) xor_permute(f[c & 1][i], m & 3);
-                        split_store(f[c & 1][i], slot + (uint32_t)g * 4096u + (uint32_t)a * 128u + (uint32_t)r7 * 16u);
-                        if (!tile && ag == 0) {
-                            // the 128-byte staging line (row m, groups 4 i'..4 i'+3) is in
-                            // registers: drop it from L2 without write-back
-                            const float* pl = src0 + 2 * (((uint64_t)m << 7) + 16u * (uint32_t)(ib + i));
-                            asm volatile("discard.global.L2 [%0], 128;" ::"l"(pl) : "memory");
-                        }
+                        const uint32_t at = slot + (uint32_t)g * 4096u + (uint32_t)a * 128u + (uint32_t)r7 * 16u;
+                        sts128(at, w[i][0], w[i][1], w[i][2], w[i][3]);
+                        sts128(at + kSplitBytes, w[i][4], w[i][5], w[i][6], w[i][7]);
+                        sts128(at + 2u * kSplitBytes, w[i][8], w[i][9], w[i][10], w[i][11]);
                     }
-                    if (c + 2 < kChunks) issue(c + 2, f[c & 1]);
+                    if (!tile) {
+                        // the chunk's 32 staging rows are consumed: drop their 256 lines
+                        // from L2 without write-back (one per loader thread)
+                        const int ln = 32 * warp + lane;
+                        const float2* pl =
+                            tab.stage + ((size_t)(xt % kSlots) * kT + xl) * kN + (size_t)(32 * c + (ln >> 3)) * kT + 16 * (ln & 7);
+                        asm volatile("discard.global.L2 [%0], 128;" ::"l"(pl) : "memory");
+                    }
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                mbar_arrive(su32(&bar_full[c]));
-                if (stop) break; // the end marker travels with chunk 0
+                __syncwarp();
+                if (lane == 0) mbar_arrive(su32(&op_full[os]));
+                if (stop) {
+                    quit = true; // the end marker has been passed on with chunk 0
+                    break;
+                }
             }
-            if (stop || broke) break;
-            ++L;
+            if (quit) break;
         }
     } else if (warp < kMmaWarp) {
         // ============================================================ epilogue
-        const int q = warp & 3, et = t - kLoadThreads;
+        // warp e = warp - 8: TMEM lanes 32 q .. 32 q + 31 (q = warp & 3),
+        // accumulator columns 128 h .. 128 h + 127 (h = e >> 2)
+        const int q = warp & 3, hcol = (warp - kLoadWarps) >> 2;
         const float scale = 1.0f / (float)kN;
-        for (uint32_t L = 0;; ++L) {
-            const uint32_t b = L & 1;
-            if (et == 0) {
-                const bool ok = mbar_wait(su32(&bar_tfull[b]), (L >> 1) & 1, &s_abort);
-                int job = ok ? s_jobq[L & 7] : -1;
-                if (!ok) {
+        for (uint32_t J = 0;; ++J) {
+            const uint32_t b = J & 1;
+            int job = -1;
+            if (lane == 0) {
+                if (mbar_wait(su32(&t_full[b]), (J >> 1) & 1, &s_abort)) {
+                    job = s_jobq[J & 7];
+                    if (job >= 0) {
+                        const int r = job / kPerRound, j = job % kPerRound;
+                        // a tile job may overwrite its staging slot once the row jobs
+                        // of the x-tile that used it before have read it
+                        if (j < kT && r >= kSlots && !wait_count(tab.done2 + (r - kSlots), kDoneTarget, &s_abort)) {
+                            report_status(st, PTDR_ERR_TIMEOUT);
+                            s_abort = 1;
+                            job = -1;
+                        }
+                    }
+                } else {
                     report_status(st, PTDR_ERR_TIMEOUT);
                     s_abort = 1;
                 }
-                if (job >= 0) {
-                    const int r = job / kPerRound, j = job % kPerRound;
-                    // a tile job may overwrite its staging slot once the row jobs
-                    // of the x-tile that used it before have read it
-                    if (j < kT && r >= kSlots && !wait_count(tab.done2 + (r - kSlots), kT, &s_abort)) {
-                        report_status(st, PTDR_ERR_TIMEOUT);
-                        s_abort = 1;
-                        job = -1;
-                    }
-                }
-                s_epi_job = job;
             }
-            named_sync(kBarEpi, kEpiThreads);
-            const int job = s_epi_job;
+            job = __shfl_sync(0xffffffffu, job, 0);
             if (job < 0) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const int r = job / kPerRound, j = job % kPerRound;
-            const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + 256u * b;
+            const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + 256u * b + 128u * hcol;
             if (j < kT) {
-                // tile job: lane = zl, columns n = 2 xl + ri
+                // tile job: lane = zl, columns n = 2 xl + re/im (xl = 64 h + n / 2)
                 const int xt = r, cb = j, zl = 32 * q + lane;
                 float2* stage = tab.stage + (size_t)(xt % kSlots) * kT * kN + (size_t)(kT * cb + zl);
 #pragma unroll 1
-                for (int cc = 0; cc < 8; ++cc) {
+                for (int cc = 0; cc < 4; ++cc) {
                     uint32_t v[32];
                     TC_LD32(v, tbase + 32u * cc);
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    if (cc == 3) {
+                        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(su32(&t_empty[b]));
+                    }
 #pragma unroll
                     for (int u = 0; u < 16; ++u) {
-                        const int xl = 16 * cc + u;
-                        const float sg = (__popc(zl & xl) & 1) ? -1.0f : 1.0f;
-                        __stcg(stage + (size_t)xl * kN, make_float2(sg * __uint_as_float(v[2 * u]), sg * __uint_as_float(v[2 * u + 1])));
+                        const int xlv = 64 * hcol + 16 * cc + u;
+                        const uint32_t sg = (uint32_t)(__popc(zl & xlv) & 1) << 31;
+                        __stcg(stage + (size_t)xlv * kN,
+                               make_float2(__uint_as_float(v[2 * u] ^ sg), __uint_as_float(v[2 * u + 1] ^ sg)));
                     }
                 }
             } else {
-                // row job: lane = zb, columns n = 2 zl + ri
-                const int xt = r - 1, xl = j - kT, zb = 32 * q + lane;
+                // row job (transposed product): lane = n - 128 h = 2 (zl - 64 h) + ri,
+                // columns zb; each store instruction covers 16 complex outputs
+                const int xt = r - 1, xl = j - kT;
                 const int x = kT * xt + xl;
-                float* out = reinterpret_cast<float*>(C + ((uint64_t)x << kLog) + (uint64_t)(kT * zb));
+                const int ri = lane & 1, zl = 64 * hcol + 16 * q + (lane >> 1);
+                const int pzl = __popc(xl & zl);
+                float* out = reinterpret_cast<float*>(C + ((uint64_t)x << kLog)) + 2 * zl + ri;
 #pragma unroll 1
-                for (int cc = 0; cc < 8; ++cc) {
+                for (int cc = 0; cc < 4; ++cc) {
                     uint32_t v[32];
                     TC_LD32(v, tbase + 32u * cc);
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    if (cc == 3) {
+                        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(su32(&t_empty[b]));
+                    }
 #pragma unroll
-                    for (int h = 0; h < 4; ++h) {
-                        float o[8];
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const int zl = 16 * cc + 4 * h + u;
-                            const float2 w = make_float2(__uint_as_float(v[8 * h + 2 * u]), __uint_as_float(v[8 * h + 2 * u + 1]));
-                            const float2 c2 = phase_neg_i(w, __popc(x & (kT * zb + zl)) & 3, scale);
-                            o[2 * u] = c2.x;
-                            o[2 * u + 1] = c2.y;
-                        }
-                        const int zl0 = 16 * cc + 4 * h;
-                        if (in_bounds(st, ((uint64_t)x << kLog) + (uint64_t)(kT * zb + zl0 + 3), lim))
-                            st8_cs(out + 2 * zl0, o);
+                    for (int u = 0; u < 32; ++u) {
+                        const int zb = 32 * cc + u;
+                        const uint32_t own = v[u];
+                        const uint32_t other = __shfl_xor_sync(0xffffffffu, own, 1);
+                        const int p = (__popc(xt & zb) + pzl) & 3;
+                        // (-i)^p: odd p swaps re and im; the sign bit of re is p bit 1,
+                        // of im (p bit 0) xor (p bit 1)
+                        const uint32_t val = (p & 1) ? other : own;
+                        const uint32_t neg = ri ? (uint32_t)((p ^ (p >> 1)) & 1) : (uint32_t)((p >> 1) & 1);
+                        const float o = __uint_as_float(val ^ (neg << 31)) * scale;
+                        if (in_bounds(st, ((uint64_t)x << kLog) + (uint64_t)(kT * zb + zl), lim))
+                            __stcs(out + 2 * kT * zb, o);
                     }
                 }
             }
-            // the accumulator is in registers and stored: hand it back to the MMA warp
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            mbar_arrive(su32(&bar_tempty[b]));
-            named_sync(kBarEpi, kEpiThreads);
-            if (et == 0) {
+            __syncwarp();
+            if (lane == 0) {
                 __threadfence();
                 atomicAdd((j < kT ? tab.done1 + r : tab.done2 + (r - 1)), 1);
             }
         }
-    } else {
+    } else if (warp == kMmaWarp) {
         // ============================================================ MMA issue
-        // M = 128, N = 256, A = bf16 K-major (H), B = bf16 MN-major, D = f32
-        const uint32_t idesc =
+        // tile jobs: M = 128 (zl), N = 256, A = H (K-major), B = operand (MN-major)
+        const uint32_t idesc_tile =
             (1u << 4) | (1u << 7) | (1u << 10) | (1u << 16) | ((256u >> 3) << 17) | ((128u >> 4) << 24);
+        // row jobs: M = 128 (half of the 256 operand columns), N = 128 (zb),
+        // A = operand (MN-major), B = H (K-major)
+        const uint32_t idesc_row =
+            (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
         bool issued = false;
-        for (uint32_t L = 0;; ++L) {
-            const uint32_t b = L & 1;
-            bool quit = false;
-            for (int c = 0; c < kChunks && !quit; ++c) {
-                int go = 1;
+        uint32_t Q = 0;
+        for (uint32_t J = 0;; ++J) {
+            const uint32_t b = J & 1;
+            bool quit = false, tile = true;
+            for (int c = 0; c < kChunks; ++c, ++Q) {
+                const uint32_t os = Q % kOpSlots;
+                int go = 1, tl = 1;
                 if (lane == 0) {
-                    bool ok = mbar_wait(su32(&bar_full[c]), L & 1, &s_abort);
+                    bool ok = mbar_wait(su32(&op_full[os]), (Q / kOpSlots) & 1, &s_abort);
                     if (ok && c == 0) {
-                        if (s_jobq[L & 7] < 0) {
+                        const int job = s_jobq[J & 7];
+                        if (job < 0) {
                             go = 0; // end of work: pass the marker on to the epilogue
-                            mbar_arrive(su32(&bar_tfull[b]));
-                        } else if (L >= 2) {
-                            ok = mbar_wait(su32(&bar_tempty[b]), ((L >> 1) - 1) & 1, &s_abort);
+                            mbar_arrive(su32(&t_full[b]));
+                        } else {
+                            tl = (job % kPerRound) < kT;
+                            if (J >= 2) ok = mbar_wait(su32(&t_empty[b]), ((J >> 1) - 1) & 1, &s_abort);
                         }
                     }
                     if (!ok) {
@@ -506,34 +609,48 @@ __global__ void __launch_bounds__(kThreads, 1)
                         go = 0;
                     }
                 }
-                go = __shfl_sync(0xffffffffu, go, 0);
-                if (!go) {
+                if (!__shfl_sync(0xffffffffu, go, 0)) {
                     quit = true;
                     break;
                 }
+                if (c == 0) tile = __shfl_sync(0xffffffffu, tl, 0) != 0;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 if (lane == 0) {
-                    const uint32_t slot = ring_a + (uint32_t)c * kChunkSmem;
+                    const uint32_t slot = op_a + os * kChunkSmem;
+                    const uint32_t dt = tmem + 256u * b;
 #pragma unroll
                     for (int kk = 0; kk < 2; ++kk) {
-                        const uint64_t da = sdesc(h_a + (uint32_t)(2 * c + kk) * 256u, 128u, 2048u);
+                        const uint64_t dh = sdesc(h_a + (uint32_t)(2 * c + kk) * 256u, 128u, 2048u);
 #pragma unroll
                         for (int s = 0; s < 3; ++s) {
-                            const uint64_t db = sdesc(slot + (uint32_t)s * kSplitBytes + (uint32_t)kk * 8192u, 4096u, 128u);
                             const uint32_t acc = (c | kk | s) ? 1u : 0u;
-                            asm volatile(
-                                "{ .reg .pred p; setp.ne.u32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(
-                                    tmem + 256u * b),
-                                "l"(da), "l"(db), "r"(idesc), "r"(acc)
-                                : "memory");
+                            const uint32_t opk = slot + (uint32_t)s * kSplitBytes + (uint32_t)kk * 8192u;
+                            if (tile) {
+                                const uint64_t db = sdesc(opk, 4096u, 128u);
+                                asm volatile(
+                                    "{ .reg .pred p; setp.ne.u32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(
+                                        dt),
+                                    "l"(dh), "l"(db), "r"(idesc_tile), "r"(acc)
+                                    : "memory");
+                            } else {
+#pragma unroll
+                                for (int h = 0; h < 2; ++h) {
+                                    const uint64_t da = sdesc(opk + 2048u * h, 4096u, 128u);
+                                    asm volatile(
+                                        "{ .reg .pred p; setp.ne.u32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(
+                                            dt + 128u * h),
+                                        "l"(da), "l"(dh), "r"(idesc_row), "r"(acc)
+                                        : "memory");
+                                }
+                            }
                         }
                     }
                     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                                     su32(&bar_empty[c]))
+                                     su32(&op_empty[os]))
                                  : "memory");
                     if (c == kChunks - 1)
                         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                                         su32(&bar_tfull[b]))
+                                         su32(&t_full[b]))
                                      : "memory");
                     issued = true;
                 }
@@ -546,11 +663,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                              su32(&bar_exit))
                          : "memory");
-            if (!mbar_wait(su32(&bar_exit), 0, &s_abort)) {
-                // s_abort may be set: wait again without it, still bounded
-                const unsigned long long t0 = now_ns();
-                while (!mbar_try(su32(&bar_exit), 0) && now_ns() - t0 < kWaitNs) {
-                }
+            const unsigned long long t0 = now_ns();
+            while (!mbar_try(su32(&bar_exit), 0) && now_ns() - t0 < kWaitNs) {
             }
         }
         __syncwarp();
@@ -580,7 +694,7 @@ cudaError_t launch_tc14_pipe(const void* A, void* C, void* ws, unsigned int* st,
     if (grid == 0) {
         int sms = 0;
         if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        grid = sms; // one CTA per SM: the ring fills shared memory and all 512 TMEM columns are held
+        grid = sms; // one CTA per SM: the rings fill shared memory and all 512 TMEM columns are held
         std::lock_guard<std::mutex> lk(mu);
         grid_for[dev & 127] = grid;
     }

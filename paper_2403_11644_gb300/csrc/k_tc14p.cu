@@ -7,56 +7,64 @@
 // d_x[128 cb + cl] = T[cl ^ xl][cl].  The length-2^14 transform over k splits
 // into 7 bits inside a block (cl) and 7 bits across blocks (cb), and both
 // halves become products with the 128 x 128 Hadamard matrix
-// H[a][b] = (-1)^{|a & b|}:
+// H[a][b] = (-1)^{|a & b|}, stored scaled by 2^-7 (exact in bf16) so that
+// the two stages together apply the 2^-14 of the definition:
 //
 //   tile job (xt, cb):  with U[m][xl] = T[m][m ^ xl] (row m of the tile
 //     permuted by XOR with m) and (-1)^{|zl & (m ^ xl)|} =
 //     (-1)^{|zl & m|} (-1)^{|zl & xl|},
-//       D'[xl][zl] = sum_cl (-1)^{|zl & cl|} T[cl ^ xl][cl]
-//                  = (-1)^{|zl & xl|} (H U)[zl][xl],
-//     written to an L2-resident staging row S[xl][128 cb + zl];
-//   row job (x):  c_x[128 zb + zl] = 2^-14 (-i)^{|x & z|} (H B)[zb][zl]
-//     with B[cb][zl] = S[xl][128 cb + zl].
+//       sum_cl (-1)^{|zl & cl|} T[cl ^ xl][cl] = (-1)^{|zl & xl|} (H U)[zl][xl];
+//     the staging row receives S[xl][128 cb + zl] = i^{|zl & xl|} (H U)[zl][xl];
+//   row job (x):  c_x[128 zb + zl] = (-i)^{|xt & zb|} (H B)[zb][zl],
+//     B[cb][zl] = S[xl][128 cb + zl].
+// The phase of the definition, (-i)^{|x & z|} with |x & z| = |xt & zb| +
+// |xl & zl|, times the sign (-1)^{|zl & xl|} of the tile stage is
+// (-i)^{|xt & zb|} i^{|xl & zl|}: the factor that depends on (xl, zl) is
+// applied where each thread holds one zl and a run of xl (tile epilogue), the
+// factor that depends on zb alone where it is the same for a whole warp (row
+// epilogue).
 //
-// Each job is one tcgen05 product D = H_128 * B (M = 128, K = 128, N = 256
-// real columns: n = 2 * column + re/im) accumulated in float32 in tensor
-// memory.  The float32 operand is split exactly into three bf16 parts by
-// truncation (hi = top 16 bits of x, mid = top 16 bits of x - hi, lo =
-// x - hi - mid, which has at most 8 significant bits), so the only rounding
-// of the tensor-core stage is the float32 accumulation; H is exact in bf16.
+// Each job is one tcgen05 product accumulated in float32 in tensor memory
+// (K = 128, taken in 4 chunks of 32).  Tile jobs: D = H U, M = zl, N = 256
+// real columns n = 2 xl + re/im, so a warp's lanes are consecutive zl and each
+// staging store covers 256 contiguous bytes.  Row jobs: the transposed
+// product D^T = B^T H in two halves of M = 128 (the real parts of the 128 zl,
+// then the imaginary parts), N = zb, so a thread holds the real and the
+// imaginary part of the same output and a warp's lanes are 32 consecutive
+// outputs of one row of C.  The float32 operand is split exactly into three
+// bf16 parts by truncation (hi = top 16 bits of x, mid = top 16 bits of
+// x - hi, lo = x - hi - mid, which has at most 8 significant bits), so the
+// only rounding of the tensor-core stage is the float32 accumulation; H is
+// exact in bf16.
 //
 // One persistent CTA per SM, warp-specialised, every hand-off an mbarrier:
 //   warp 17     producer: takes jobs from the queue and copies each K chunk
 //               (32 rows of 1 KiB: tile rows from HBM, staging rows from L2)
 //               with bulk asynchronous copies into a 3-deep ring of padded
-//               raw buffers (row pitch 1040 bytes);
-//   warps 0-7   loaders: raw float32 rows from shared memory, the XOR
-//               permutation (tile jobs), the split, and 16-byte stores into
-//               the MN-major core matrices of a 2-deep operand ring;
+//               raw buffers (row pitch 1040 bytes: conflict-free reads);
+//   warps 0-7   loaders: raw float32 rows from shared memory (tile jobs read
+//               each complex value at its XOR-permuted column), the split,
+//               and 16-byte stores into the MN-major core matrices of a
+//               2-deep operand ring;
 //   warp 16     one lane issues the MMAs of each chunk and commits the chunk
 //               back to the ring and each job to one of two tensor-memory
 //               accumulators (2 x 256 columns);
-//   warps 8-15  epilogue: tcgen05.ld of the accumulator, sign or phase and
-//               scale, coalesced stores.
-// Tile jobs compute D = H * U (M = zl, N = (xl, re/im)): a warp's lanes are
-// consecutive zl, so each staging store covers 256 contiguous bytes.  Row
-// jobs compute the transposed product D^T = B^T * H (M = (zl, re/im) in two
-// halves of 128, N = zb) so that a warp's lanes are 16 consecutive complex
-// outputs: one 128-byte line of C per store; the (-i)^{|x&z|} re/im swap
-// takes the partner lane's value by shuffle.
+//   warps 8-15  epilogue: tcgen05.ld of the accumulator, phase, coalesced
+//               stores.
 // So the copies of one job, the split of the next chunk, the MMAs and the
 // epilogue of the job before overlap on each SM.
 //
 // Jobs come from one atomic queue in x-tile-major rounds: round r holds the
-// 128 tile jobs of x-tile r, then the 128 row jobs of x-tile r-1.  A row job
-// waits (bounded) until its x-tile's tile jobs are done; a tile job waits
-// (bounded) before writing its staging slot until the row jobs of the x-tile
-// that used the slot before are done (each epilogue warp counts itself, so a
-// finished x-tile pass is 128 jobs x 8 warps).  Within a CTA every stage waits only
-// on older jobs, so the earliest unfinished job can always proceed.  Every
-// wait is bounded: on time-out the kernel records PTDR_ERR_TIMEOUT, each
-// role leaves its loop, in-flight MMAs are awaited (bounded) and the tensor
-// memory is released.
+// 128 tile jobs of x-tile r, then the 128 row jobs of x-tile r - 2 (two
+// rounds of slack, so that a row job rarely finds its x-tile unfinished).  A
+// row job waits (bounded) until its x-tile's tile jobs are done; a tile job
+// waits (bounded) before writing its staging slot until the row jobs of the
+// x-tile that used the slot before are done (each epilogue warp counts
+// itself, so a finished x-tile pass is 128 jobs x 8 warps).  Within a CTA
+// every stage waits only on older jobs, so the earliest unfinished job can
+// always proceed.  Every wait is bounded: on time-out the kernel records
+// PTDR_ERR_TIMEOUT, each role leaves its loop, in-flight MMAs are awaited
+// (bounded) and the tensor memory is released.
 #include <cuda_bf16.h>
 
 #include <mutex>
@@ -78,11 +86,11 @@ constexpr int kMmaWarp = kLoadWarps + kEpiWarps; // 16
 constexpr int kProdWarp = kMmaWarp + 1;          // 17
 constexpr int kThreads = (kProdWarp + 1) * 32;   // 576
 constexpr int kChunks = 4;                        // K chunks of 32 rows per job
-constexpr uint32_t kSplitBytes = 32u * 256u * 2u; // one split of a chunk: 32 K x 256 N bf16
+constexpr uint32_t kSplitBytes = 32u * 256u * 2u; // one split of a chunk: 32 K x 256 M/N bf16
 constexpr uint32_t kChunkSmem = 3u * kSplitBytes; // 48 KiB operand chunk
 constexpr int kOpSlots = 2;
 constexpr int kRawSlots = 3;
-constexpr uint32_t kRawPitch = 1040u;            // 1 KiB row + 16 bytes: conflict-free 8-row reads
+constexpr uint32_t kRawPitch = 1040u;            // 1 KiB row + 16 bytes
 constexpr uint32_t kRawSlotBytes = 32u * kRawPitch;
 constexpr uint32_t kRawOff = kOpSlots * kChunkSmem;
 constexpr uint32_t kHOff = kRawOff + kRawSlots * kRawSlotBytes;
@@ -90,11 +98,14 @@ constexpr uint32_t kHBytes = kT * kT * 2u;
 constexpr uint32_t kSmemBytes = kHOff + kHBytes + 128u; // + alignment slack
 constexpr uint32_t kTmemCols = 512;                     // two 128 x 256 float32 accumulators
 constexpr int kSlots = 4;                               // staging slots (x-tiles in flight)
+constexpr int kLag = 2;                                 // row jobs of x-tile r run in round r + kLag
 constexpr int kPerRound = 2 * kT;
-constexpr int kItems = (kTiles + 1) * kPerRound;
+constexpr int kItems = (kTiles + kLag) * kPerRound;
 constexpr int kDoneTarget = kT * kEpiWarps; // epilogue warps per finished x-tile pass
 constexpr unsigned long long kWaitNs = 1000000000ull; // bound of every wait: 1 s
+constexpr uint16_t kHPos = 0x3C00u, kHNeg = 0xBC00u;  // +2^-7, -2^-7 in bf16
 
+static_assert(kSlots >= kLag + 2, "a staging slot is rewritten only after its row jobs were dequeued");
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -198,47 +209,50 @@ __device__ __forceinline__ void sts128(uint32_t addr, uint32_t a, uint32_t b, ui
     asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
 }
 
-// Upper 16 bits of a and b as one bf16x2 word (element 0 in the low half).
-__device__ __forceinline__ uint32_t hi16x2(float a, float b)
+__device__ __forceinline__ void lds64(uint32_t addr, float& a, float& b)
 {
-    return __byte_perm(__float_as_uint(a), __float_as_uint(b), 0x7632);
+    asm volatile("ld.shared.v2.f32 {%0,%1}, [%2];" : "=f"(a), "=f"(b) : "r"(addr));
 }
 
 __device__ __forceinline__ float trunc_bf16(float a) { return __uint_as_float(__float_as_uint(a) & 0xFFFF0000u); }
 
-// Exact three-way split of 8 floats into bf16 parts, packed as three 16-byte
-// core-matrix rows: w[0..3] = hi, w[4..7] = mid, w[8..11] = lo.
-__device__ __forceinline__ void split3(const float (&f)[8], uint32_t (&w)[12])
+// (a, b) - (c, d) as one packed float32 pair operation.
+__device__ __forceinline__ void sub2(float a, float b, float c, float d, float& r0, float& r1)
 {
-    float r[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) r[k] = f[k] - trunc_bf16(f[k]);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) w[k] = hi16x2(f[2 * k], f[2 * k + 1]);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) w[4 + k] = hi16x2(r[2 * k], r[2 * k + 1]);
-#pragma unroll
-    for (int k = 0; k < 8; ++k) r[k] = r[k] - trunc_bf16(r[k]);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) w[8 + k] = hi16x2(r[2 * k], r[2 * k + 1]);
+    uint64_t x, y, r;
+    asm("mov.b64 %0, {%1,%2};" : "=l"(x) : "f"(a), "f"(b));
+    asm("mov.b64 %0, {%1,%2};" : "=l"(y) : "f"(c), "f"(d));
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(x), "l"(y));
+    asm("mov.b64 {%0,%1}, %2;" : "=f"(r0), "=f"(r1) : "l"(r));
 }
 
-// v <- (v[j ^ p]) for the four complex values j = 0..3 held as 8 floats.
-__device__ __forceinline__ void xor_permute(float (&f)[8], int p)
+// Exact three-way split of the pair (a, b) into bf16x2 words (a in the low
+// half): hi = top 16 bits, mid = top 16 bits of the remainder, lo = the rest.
+// Each remainder x - trunc(x) is exact in float32 (same sign and exponent).
+__device__ __forceinline__ void split3(float a, float b, uint32_t& hi, uint32_t& mid, uint32_t& lo)
 {
-    float g[8];
-    const bool s1 = (p & 1) != 0, s2 = (p & 2) != 0;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        g[2 * j] = s1 ? f[2 * (j ^ 1)] : f[2 * j];
-        g[2 * j + 1] = s1 ? f[2 * (j ^ 1) + 1] : f[2 * j + 1];
-    }
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        f[2 * j] = s2 ? g[2 * (j ^ 2)] : g[2 * j];
-        f[2 * j + 1] = s2 ? g[2 * (j ^ 2) + 1] : g[2 * j + 1];
-    }
+    hi = __byte_perm(__float_as_uint(a), __float_as_uint(b), 0x7632);
+    float ra, rb, la, lb;
+    sub2(a, b, trunc_bf16(a), trunc_bf16(b), ra, rb);
+    mid = __byte_perm(__float_as_uint(ra), __float_as_uint(rb), 0x7632);
+    sub2(ra, rb, trunc_bf16(ra), trunc_bf16(rb), la, lb);
+    lo = __byte_perm(__float_as_uint(la), __float_as_uint(lb), 0x7632);
 }
+
+// Job number -> kind, x-tile and column block (tile job) or mask (row job).
+// Round r holds the tile jobs of x-tile r, then the row jobs of x-tile
+// r - kLag; slots past either end of the x-tile range are empty (false).
+__device__ __forceinline__ bool decode(int job, bool& tile, int& xt, int& idx)
+{
+    const int r = job / kPerRound, j = job % kPerRound;
+    tile = j < kT;
+    xt = tile ? r : r - kLag;
+    idx = tile ? j : j - kT;
+    return xt >= 0 && xt < kTiles;
+}
+
+// Sign bit of bit k of a mask, moved to bit 31.
+__device__ __forceinline__ uint32_t sgn(uint32_t mask, int k) { return (mask << (31 - k)) & 0x80000000u; }
 
 #define TC_LD32(r, addr)                                                                              \
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "                                            \
@@ -255,8 +269,8 @@ __device__ __forceinline__ void xor_permute(float (&f)[8], int p)
 
 struct TcPipeTables {
     int* head;     // work-queue counter
-    int* done1;    // tile jobs finished per x-tile
-    int* done2;    // row jobs finished per x-tile
+    int* done1;    // tile jobs finished per x-tile (x 8 epilogue warps)
+    int* done2;    // row jobs finished per x-tile (x 8 epilogue warps)
     float2* stage; // kSlots x 128 rows x 2^14
 };
 
@@ -276,11 +290,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint16_t* hmat = reinterpret_cast<uint16_t*>(smem_raw + (h_a - raw_a));
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
 
-    // H_128 in K-major core matrices (A operand of tile jobs, B operand of
-    // row jobs; H is symmetric): element (r, k) = (-1)^{|r & k|}
+    // 2^-7 H_128 in K-major core matrices (A operand of tile jobs, B operand
+    // of row jobs; H is symmetric): element (r, k) = 2^-7 (-1)^{|r & k|}
     for (int e = t; e < kT * kT; e += kThreads) {
         const int z = e >> 7, k = e & 127;
-        hmat[((z >> 3) * 16 + (k >> 3)) * 64 + (z & 7) * 8 + (k & 7)] = (__popc(z & k) & 1) ? 0xBF80u : 0x3F80u;
+        hmat[((z >> 3) * 16 + (k >> 3)) * 64 + (z & 7) * 8 + (k & 7)] = (__popc(z & k) & 1) ? kHNeg : kHPos;
     }
     if (warp == kMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&s_tmem)),
@@ -324,20 +338,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             job = __shfl_sync(0xffffffffu, job, 0);
             bool tile = false;
-            int xt = 0, cb = 0, xl = 0;
-            if (job < kItems) {
-                const int r = job / kPerRound, j = job % kPerRound;
-                tile = j < kT;
-                if (tile) {
-                    xt = r;
-                    cb = j;
-                    if (xt >= kTiles) continue; // empty slot of the last round
-                } else {
-                    xt = r - 1;
-                    xl = j - kT;
-                    if (xt < 0) continue; // empty slot of the first round
-                }
-            }
+            int xt = 0, idx = 0;
+            if (job < kItems && !decode(job, tile, xt, idx)) continue; // empty slot of the first or last rounds
             int ok = 1;
             if (lane == 0 && job < kItems && !tile && !wait_count(tab.done1 + xt, kDoneTarget, &s_abort)) {
                 report_status(st, PTDR_ERR_TIMEOUT);
@@ -363,6 +365,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 asm volatile("fence.proxy.async;" ::: "memory");
             }
             if (lane == 0) s_jobq[J & 7] = job;
+            const int cb = idx, xl = idx;
             const char* src0 =
                 tile ? reinterpret_cast<const char*>(A + ((uint64_t)(kT * (cb ^ xt)) << kLog) + (uint64_t)(kT * cb))
                      : reinterpret_cast<const char*>(tab.stage + ((size_t)(xt % kSlots) * kT + xl) * kN);
@@ -396,11 +399,20 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else if (warp < kLoadWarps) {
         // ============================================================ loaders
-        // warp w: rows 8 g + (lane & 7) of each chunk, g = w >> 1, and N groups
-        // a = 4 (ib + i) + (lane >> 3), ib = 4 (w & 1).  A warp instruction
-        // covers 8 rows x 4 N groups: 4 conflict-free wavefronts for the raw
-        // reads (pitch 1040) and for the operand stores.
-        const int g = warp >> 1, ib = 4 * (warp & 1), r7 = lane & 7, ag = lane >> 3;
+        // Warp w takes K rows 8 g + (lane & 7) of each chunk, g = w >> 1.
+        // Tile job (B operand, N = 2 xl + re/im): N groups a = 4 (ib + i) + (lane >> 3),
+        //   i = 0..3, ib = 4 (w & 1); group a is xl = 4a .. 4a + 3, whose values in
+        //   tile row m sit at columns m ^ xl = 4 (a ^ (m >> 2)) + ((m & 3) ^ j).
+        // Row job (A operand, M = real parts of zl = 0..127, then imaginary parts):
+        //   units v = ub + u, u = 0, 1, ub = 8 (w & 1) + 2 (lane >> 3); unit v is
+        //   zl = 8v .. 8v + 7 (64 contiguous raw bytes), stored as M group v (real
+        //   parts) and M group 16 + v (imaginary parts).
+        // In each 8-lane phase of a warp instruction the lanes cover 8 distinct rows,
+        // so raw reads (pitch 1040) and operand stores (128-byte core matrices) are
+        // conflict-free.
+        const int g = warp >> 1, r7 = lane & 7, ag = lane >> 3;
+        const int ib = 4 * (warp & 1), ub = 8 * (warp & 1) + 2 * ag;
+        const uint32_t pj = (uint32_t)(r7 & 3); // m & 3 for every row this thread reads
         uint32_t Q = 0;
         for (uint32_t J = 0;; ++J) {
             int job = -1;
@@ -415,32 +427,34 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const bool stop = job < 0;
                 bool tile = false;
                 int xt = 0, xl = 0;
-                if (!stop) {
-                    const int r = job / kPerRound, j = job % kPerRound;
-                    tile = j < kT;
-                    xt = tile ? r : r - 1;
-                    xl = j - kT;
-                }
-                // raw rows -> registers
-                float f[4][8];
+                if (!stop) (void)decode(job, tile, xt, xl);
                 const uint32_t rrow = rawb_a + rs * kRawSlotBytes + (uint32_t)(8 * g + r7) * kRawPitch;
-                const int m = 32 * c + 8 * g + r7;
-                if (!stop) {
+                uint32_t w[48];
+                if (!stop && tile) {
+                    const int mh = (32 * c + 8 * g + r7) >> 2;
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
-                        const int a = 4 * (ib + i) + ag;
-                        const int as = tile ? (a ^ (m >> 2)) : a;
-                        lds128(rrow + (uint32_t)as * 32u, f[i][0], f[i][1], f[i][2], f[i][3]);
-                        lds128(rrow + (uint32_t)as * 32u + 16u, f[i][4], f[i][5], f[i][6], f[i][7]);
+                        const uint32_t gb = rrow + 32u * (uint32_t)((4 * (ib + i) + ag) ^ mh);
+                        float f[8];
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) lds64(gb + 8u * (pj ^ (uint32_t)j), f[2 * j], f[2 * j + 1]);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k)
+                            split3(f[2 * k], f[2 * k + 1], w[12 * i + k], w[12 * i + 4 + k], w[12 * i + 8 + k]);
                     }
-                }
-                // permute and split in registers; the raw slot is free after this
-                uint32_t w[4][12];
-                if (!stop) {
+                } else if (!stop) {
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        if (tile) xor_permute(f[i], r7 & 3);
-                        split3(f[i], w[i]);
+                    for (int u = 0; u < 2; ++u) {
+                        const uint32_t vb = rrow + 64u * (uint32_t)(ub + u);
+                        float f[16]; // re0, im0, re1, im1, ...
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) lds128(vb + 16u * k, f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            split3(f[4 * k], f[4 * k + 2], w[24 * u + k], w[24 * u + 4 + k], w[24 * u + 8 + k]);
+                            split3(f[4 * k + 1], f[4 * k + 3], w[24 * u + 12 + k], w[24 * u + 16 + k],
+                                   w[24 * u + 20 + k]);
+                        }
                     }
                 }
                 __syncwarp();
@@ -451,24 +465,34 @@ __global__ void __launch_bounds__(kThreads, 1)
                     quit = true;
                     break;
                 }
-                if (!stop) {
-                    const uint32_t slot = op_a + os * kChunkSmem;
+                const uint32_t slot = op_a + os * kChunkSmem + (uint32_t)g * 4096u + (uint32_t)r7 * 16u;
+                if (!stop && tile) {
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
-                        const int a = 4 * (ib + i) + ag;
-                        const uint32_t at = slot + (uint32_t)g * 4096u + (uint32_t)a * 128u + (uint32_t)r7 * 16u;
-                        sts128(at, w[i][0], w[i][1], w[i][2], w[i][3]);
-                        sts128(at + kSplitBytes, w[i][4], w[i][5], w[i][6], w[i][7]);
-                        sts128(at + 2u * kSplitBytes, w[i][8], w[i][9], w[i][10], w[i][11]);
+                        const uint32_t at = slot + (uint32_t)(4 * (ib + i) + ag) * 128u;
+#pragma unroll
+                        for (int s = 0; s < 3; ++s)
+                            sts128(at + (uint32_t)s * kSplitBytes, w[12 * i + 4 * s], w[12 * i + 4 * s + 1],
+                                   w[12 * i + 4 * s + 2], w[12 * i + 4 * s + 3]);
                     }
-                    if (!tile) {
-                        // the chunk's 32 staging rows are consumed: drop their 256 lines
-                        // from L2 without write-back (one per loader thread)
-                        const int ln = 32 * warp + lane;
-                        const float2* pl =
-                            tab.stage + ((size_t)(xt % kSlots) * kT + xl) * kN + (size_t)(32 * c + (ln >> 3)) * kT + 16 * (ln & 7);
-                        asm volatile("discard.global.L2 [%0], 128;" ::"l"(pl) : "memory");
+                } else if (!stop) {
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        const uint32_t at = slot + (uint32_t)(ub + u) * 128u;
+#pragma unroll
+                        for (int s = 0; s < 3; ++s) {
+                            sts128(at + (uint32_t)s * kSplitBytes, w[24 * u + 4 * s], w[24 * u + 4 * s + 1],
+                                   w[24 * u + 4 * s + 2], w[24 * u + 4 * s + 3]);
+                            sts128(at + 2048u + (uint32_t)s * kSplitBytes, w[24 * u + 12 + 4 * s],
+                                   w[24 * u + 13 + 4 * s], w[24 * u + 14 + 4 * s], w[24 * u + 15 + 4 * s]);
+                        }
                     }
+                    // the chunk's 32 staging rows are consumed: drop their 256 lines
+                    // from L2 without write-back (one per loader thread)
+                    const int ln = 32 * warp + lane;
+                    const float2* pl =
+                        tab.stage + ((size_t)(xt % kSlots) * kT + xl) * kN + (size_t)(32 * c + (ln >> 3)) * kT + 16 * (ln & 7);
+                    asm volatile("discard.global.L2 [%0], 128;" ::"l"(pl) : "memory");
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncwarp();
@@ -482,25 +506,37 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else if (warp < kMmaWarp) {
         // ============================================================ epilogue
-        // warp e = warp - 8: TMEM lanes 32 q .. 32 q + 31 (q = warp & 3),
-        // accumulator columns 128 h .. 128 h + 127 (h = e >> 2)
+        // warp e = warp - 8 reads TMEM lanes 32 q .. 32 q + 31 (q = warp & 3, the
+        // lanes its warp slot may access) and accumulator columns of half h = e >> 2.
         const int q = warp & 3, hcol = (warp - kLoadWarps) >> 2;
-        const float scale = 1.0f / (float)kN;
+        const int zl = 32 * q + lane;
+        // Tile jobs: i^{|xl & zl|} for this thread's zl and the 64 xl = 64 h + k of its
+        // columns; bit k & 31 of word k >> 5 in three masks: odd power (re/im swap),
+        // sign of the real part (power 1, 2), sign of the imaginary part (power 2, 3).
+        uint32_t t_odd[2] = {0u, 0u}, t_sx[2] = {0u, 0u}, t_sy[2] = {0u, 0u};
+#pragma unroll
+        for (int k = 0; k < 64; ++k) {
+            const uint32_t ph = (uint32_t)__popc((64 * hcol + k) & zl) & 3u;
+            const uint32_t bit = 1u << (k & 31);
+            t_odd[k >> 5] |= (ph & 1u) ? bit : 0u;
+            t_sx[k >> 5] |= ((ph ^ (ph >> 1)) & 1u) ? bit : 0u;
+            t_sy[k >> 5] |= (ph & 2u) ? bit : 0u;
+        }
         for (uint32_t J = 0;; ++J) {
             const uint32_t b = J & 1;
             int job = -1;
             if (lane == 0) {
                 if (mbar_wait(su32(&t_full[b]), (J >> 1) & 1, &s_abort)) {
                     job = s_jobq[J & 7];
-                    if (job >= 0) {
-                        const int r = job / kPerRound, j = job % kPerRound;
-                        // a tile job may overwrite its staging slot once the row jobs
-                        // of the x-tile that used it before have read it
-                        if (j < kT && r >= kSlots && !wait_count(tab.done2 + (r - kSlots), kDoneTarget, &s_abort)) {
-                            report_status(st, PTDR_ERR_TIMEOUT);
-                            s_abort = 1;
-                            job = -1;
-                        }
+                    bool tl = false;
+                    int xt = 0, ix = 0;
+                    // a tile job may overwrite its staging slot once the row jobs
+                    // of the x-tile that used it before have read it
+                    if (job >= 0 && decode(job, tl, xt, ix) && tl && xt >= kSlots &&
+                        !wait_count(tab.done2 + (xt - kSlots), kDoneTarget, &s_abort)) {
+                        report_status(st, PTDR_ERR_TIMEOUT);
+                        s_abort = 1;
+                        job = -1;
                     }
                 } else {
                     report_status(st, PTDR_ERR_TIMEOUT);
@@ -510,68 +546,85 @@ __global__ void __launch_bounds__(kThreads, 1)
             job = __shfl_sync(0xffffffffu, job, 0);
             if (job < 0) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const int r = job / kPerRound, j = job % kPerRound;
-            const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + 256u * b + 128u * hcol;
-            if (j < kT) {
-                // tile job: lane = zl, columns n = 2 xl + re/im (xl = 64 h + n / 2)
-                const int xt = r, cb = j, zl = 32 * q + lane;
-                float2* stage = tab.stage + (size_t)(xt % kSlots) * kT * kN + (size_t)(kT * cb + zl);
+            bool tile = false;
+            int xt = 0, idx = 0;
+            (void)decode(job, tile, xt, idx);
+            const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + 256u * b;
+            if (tile) {
+                // columns n = 2 xl + re/im, xl = 64 h + 16 cc + u; row S[xl] of the slot
+                const int cb = idx;
+                float2* stage = tab.stage + (size_t)(xt % kSlots) * kT * kN + (size_t)(64 * hcol) * kN +
+                                (size_t)(kT * cb + zl);
 #pragma unroll 1
                 for (int cc = 0; cc < 4; ++cc) {
                     uint32_t v[32];
-                    TC_LD32(v, tbase + 32u * cc);
+                    TC_LD32(v, tbase + 128u * hcol + 32u * cc);
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                     if (cc == 3) {
                         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                         __syncwarp();
                         if (lane == 0) mbar_arrive(su32(&t_empty[b]));
                     }
+                    // this run's 16 bits of the tables, moved to bits 0..15
+                    const int sh = 16 * (cc & 1);
+                    const uint32_t od = (cc & 2 ? t_odd[1] : t_odd[0]) >> sh;
+                    const uint32_t sx = (cc & 2 ? t_sx[1] : t_sx[0]) >> sh;
+                    const uint32_t sy = (cc & 2 ? t_sy[1] : t_sy[0]) >> sh;
+                    float2* srow = stage + (size_t)(16 * cc) * kN;
 #pragma unroll
                     for (int u = 0; u < 16; ++u) {
-                        const int xlv = 64 * hcol + 16 * cc + u;
-                        const uint32_t sg = (uint32_t)(__popc(zl & xlv) & 1) << 31;
-                        __stcg(stage + (size_t)xlv * kN,
-                               make_float2(__uint_as_float(v[2 * u] ^ sg), __uint_as_float(v[2 * u + 1] ^ sg)));
+                        const bool odd = ((od >> u) & 1u) != 0;
+                        const uint32_t ox = (odd ? v[2 * u + 1] : v[2 * u]) ^ sgn(sx, u);
+                        const uint32_t oy = (odd ? v[2 * u] : v[2 * u + 1]) ^ sgn(sy, u);
+                        __stcg(srow + (size_t)u * kN, make_float2(__uint_as_float(ox), __uint_as_float(oy)));
                     }
                 }
             } else {
-                // row job (transposed product): lane = n - 128 h = 2 (zl - 64 h) + ri,
-                // columns zb; each store instruction covers 16 complex outputs
-                const int xt = r - 1, xl = j - kT;
-                const int x = kT * xt + xl;
-                const int ri = lane & 1, zl = 64 * hcol + 16 * q + (lane >> 1);
-                const int pzl = __popc(xl & zl);
-                float* out = reinterpret_cast<float*>(C + ((uint64_t)x << kLog)) + 2 * zl + ri;
-#pragma unroll 1
-                for (int cc = 0; cc < 4; ++cc) {
-                    uint32_t v[32];
-                    TC_LD32(v, tbase + 32u * cc);
+                // real parts of zl in columns zb, imaginary parts in 128 + zb;
+                // this warp writes zb = 64 h + 32 cc + u of row x
+                const int xl = idx, x = kT * xt + xl;
+                // (-i)^{|xt & zb|}: bits u of the two low bits of popc((xt & 31) & u),
+                // accumulated over the set bits of xt & 31 (adding 1 to a 2-bit value
+                // flips bit 0 and carries bit 0 into bit 1)
+                const uint32_t m5 = (uint32_t)xt & 31u;
+                uint32_t w1 = 0u, w2 = 0u;
+                const uint32_t pat[5] = {0xAAAAAAAAu, 0xCCCCCCCCu, 0xF0F0F0F0u, 0xFF00FF00u, 0xFFFF0000u};
+#pragma unroll
+                for (int bb = 0; bb < 5; ++bb) {
+                    const uint32_t pb = ((m5 >> bb) & 1u) ? pat[bb] : 0u;
+                    w2 ^= w1 & pb;
+                    w1 ^= pb;
+                }
+                float2* out = C + ((uint64_t)x << kLog) + (uint64_t)(kT * 64 * hcol) + (uint64_t)zl;
+#pragma unroll
+                for (int cc = 0; cc < 2; ++cc) {
+                    const uint32_t bs = (uint32_t)__popc(xt & (64 * hcol + 32 * cc)) & 3u;
+                    const uint32_t odd = w1 ^ ((bs & 1u) ? 0xFFFFFFFFu : 0u);
+                    const uint32_t two = w2 ^ ((bs & 2u) ? 0xFFFFFFFFu : 0u) ^ ((bs & 1u) ? w1 : 0u);
+                    const uint32_t sx = two, sy = odd ^ two;
+                    uint32_t vr[32], vi[32];
+                    TC_LD32(vr, tbase + 64u * hcol + 32u * cc);
+                    TC_LD32(vi, tbase + 128u + 64u * hcol + 32u * cc);
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                    if (cc == 3) {
+                    if (cc == 1) {
                         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                         __syncwarp();
                         if (lane == 0) mbar_arrive(su32(&t_empty[b]));
                     }
 #pragma unroll
                     for (int u = 0; u < 32; ++u) {
-                        const int zb = 32 * cc + u;
-                        const uint32_t own = v[u];
-                        const uint32_t other = __shfl_xor_sync(0xffffffffu, own, 1);
-                        const int p = (__popc(xt & zb) + pzl) & 3;
-                        // (-i)^p: odd p swaps re and im; the sign bit of re is p bit 1,
-                        // of im (p bit 0) xor (p bit 1)
-                        const uint32_t val = (p & 1) ? other : own;
-                        const uint32_t neg = ri ? (uint32_t)((p ^ (p >> 1)) & 1) : (uint32_t)((p >> 1) & 1);
-                        const float o = __uint_as_float(val ^ (neg << 31)) * scale;
-                        if (in_bounds(st, ((uint64_t)x << kLog) + (uint64_t)(kT * zb + zl), lim))
-                            __stcs(out + 2 * kT * zb, o);
+                        const bool o = ((odd >> u) & 1u) != 0;
+                        const uint32_t ox = (o ? vi[u] : vr[u]) ^ sgn(sx, u);
+                        const uint32_t oy = (o ? vr[u] : vi[u]) ^ sgn(sy, u);
+                        if (in_bounds(st, ((uint64_t)x << kLog) + (uint64_t)(kT * (64 * hcol + 32 * cc + u) + zl), lim))
+                            __stcs(out + (size_t)(kT * (32 * cc + u)), make_float2(__uint_as_float(ox), __uint_as_float(oy)));
                     }
                 }
             }
             __syncwarp();
             if (lane == 0) {
                 __threadfence();
-                atomicAdd((j < kT ? tab.done1 + r : tab.done2 + (r - 1)), 1);
+                atomicAdd((tile ? tab.done1 : tab.done2) + xt, 1);
             }
         }
     } else if (warp == kMmaWarp) {
@@ -579,7 +632,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // tile jobs: M = 128 (zl), N = 256, A = H (K-major), B = operand (MN-major)
         const uint32_t idesc_tile =
             (1u << 4) | (1u << 7) | (1u << 10) | (1u << 16) | ((256u >> 3) << 17) | ((128u >> 4) << 24);
-        // row jobs: M = 128 (half of the 256 operand columns), N = 128 (zb),
+        // row jobs: M = 128 (one half of the 256 operand rows), N = 128 (zb),
         // A = operand (MN-major), B = H (K-major)
         const uint32_t idesc_row =
             (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | ((128u >> 3) << 17) | ((128u >> 4) << 24);

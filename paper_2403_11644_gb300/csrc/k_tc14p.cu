@@ -40,12 +40,14 @@
 // One persistent CTA per SM, warp-specialised, every hand-off an mbarrier:
 //   warp 17     producer: takes jobs from the queue and copies each K chunk
 //               (32 rows of 1 KiB: tile rows from HBM, staging rows from L2)
-//               with bulk asynchronous copies into a 3-deep ring of padded
-//               raw buffers (row pitch 1040 bytes: conflict-free reads);
-//   warps 0-7   loaders: raw float32 rows from shared memory (tile jobs read
-//               each complex value at its XOR-permuted column), the split,
-//               and 16-byte stores into the MN-major core matrices of a
-//               2-deep operand ring;
+//               into a 3-deep raw ring with eight tensor-map copies of
+//               32 rows x 128 bytes (128-byte swizzle), which the copy engine
+//               serves at over twice the rate of 1 KiB row copies;
+//   warps 0-7   loaders: one raw row per lane (tile jobs read each complex
+//               value at its XOR-permuted column; the swizzle keeps the eight
+//               rows of a read phase on distinct banks), the split, and
+//               16-byte stores into the MN-major core matrices of a 2-deep
+//               operand ring;
 //   warp 16     one lane issues the MMAs of each chunk and commits the chunk
 //               back to the ring and each job to one of two tensor-memory
 //               accumulators (2 x 256 columns);
@@ -65,6 +67,7 @@
 // always proceed.  Every wait is bounded: on time-out the kernel records
 // PTDR_ERR_TIMEOUT, each role leaves its loop, in-flight MMAs are awaited
 // (bounded) and the tensor memory is released.
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include <mutex>
@@ -90,12 +93,11 @@ constexpr uint32_t kSplitBytes = 32u * 256u * 2u; // one split of a chunk: 32 K 
 constexpr uint32_t kChunkSmem = 3u * kSplitBytes; // 48 KiB operand chunk
 constexpr int kOpSlots = 2;
 constexpr int kRawSlots = 3;
-constexpr uint32_t kRawPitch = 1040u;            // 1 KiB row + 16 bytes
-constexpr uint32_t kRawSlotBytes = 32u * kRawPitch;
+constexpr uint32_t kRawSlotBytes = 32u * 1024u;  // 8 swizzled boxes of 32 rows x 128 bytes
 constexpr uint32_t kRawOff = kOpSlots * kChunkSmem;
 constexpr uint32_t kHOff = kRawOff + kRawSlots * kRawSlotBytes;
 constexpr uint32_t kHBytes = kT * kT * 2u;
-constexpr uint32_t kSmemBytes = kHOff + kHBytes + 128u; // + alignment slack
+constexpr uint32_t kSmemBytes = kHOff + kHBytes + 1024u; // + alignment slack (swizzled boxes: 1 KiB)
 constexpr uint32_t kTmemCols = 512;                     // two 128 x 256 float32 accumulators
 constexpr int kSlots = 4;                               // staging slots (x-tiles in flight)
 constexpr int kLag = 2;                                 // row jobs of x-tile r run in round r + kLag
@@ -134,15 +136,15 @@ __device__ __forceinline__ bool wait_count(const int* p, int target, const volat
     return true;
 }
 
-// One test of an mbarrier phase; a waiting thread is suspended in hardware
-// (up to 20 us, woken early when the phase completes) so that polling warps
-// do not take issue slots from the working ones.
+// One test of an mbarrier phase (a potentially blocking try_wait with the
+// system's default time limit: a longer suspend hint delays the wake-up of
+// the operand-ring hand-offs).
 __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
 {
     uint32_t done;
-    asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3; selp.u32 %0, 1, 0, p; }"
+    asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
                  : "=r"(done)
-                 : "r"(bar), "r"(parity), "r"(20000u)
+                 : "r"(bar), "r"(parity)
                  : "memory");
     return done != 0;
 }
@@ -169,11 +171,13 @@ __device__ __forceinline__ void mbar_arrive_tx(uint32_t bar, uint32_t bytes)
                  : "memory");
 }
 
-// Bulk asynchronous copy global -> shared, completion counted on an mbarrier.
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar)
+// Tensor-map copy of one 2-D box global -> shared (coordinates: x = float
+// column, y = row), completion counted on an mbarrier.
+__device__ __forceinline__ void tma_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar)
 {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                 "l"(src), "r"(bytes), "r"(bar)
+    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+                     dst),
+                 "l"(map), "r"(x), "r"(y), "r"(bar)
                  : "memory");
 }
 
@@ -275,7 +279,8 @@ struct TcPipeTables {
 };
 
 __global__ void __launch_bounds__(kThreads, 1)
-    k_tc14_pipe(const float2* __restrict__ A, float2* __restrict__ C, TcPipeTables tab, unsigned int* st)
+    k_tc14_pipe(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmS, float2* __restrict__ C,
+                TcPipeTables tab, unsigned int* st)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) unsigned long long raw_full[kRawSlots], raw_empty[kRawSlots], op_full[kOpSlots],
@@ -285,7 +290,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     __shared__ uint32_t s_tmem;
 
     const uint32_t raw_a = su32(smem_raw);
-    const uint32_t base = (raw_a + 127u) & ~127u;
+    const uint32_t base = (raw_a + 1023u) & ~1023u;
     const uint32_t op_a = base, rawb_a = base + kRawOff, h_a = base + kHOff;
     uint16_t* hmat = reinterpret_cast<uint16_t*>(smem_raw + (h_a - raw_a));
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -366,10 +371,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             if (lane == 0) s_jobq[J & 7] = job;
             const int cb = idx, xl = idx;
-            const char* src0 =
-                tile ? reinterpret_cast<const char*>(A + ((uint64_t)(kT * (cb ^ xt)) << kLog) + (uint64_t)(kT * cb))
-                     : reinterpret_cast<const char*>(tab.stage + ((size_t)(xt % kSlots) * kT + xl) * kN);
-            const uint64_t pitch = tile ? ((uint64_t)kN * 8u) : (uint64_t)kT * 8u; // bytes between K rows
+            // tile job: rows 128 (cb ^ xt) + k of A, float columns 256 cb + 32 b + .;
+            // row job: staging rows (slot, xl, k) of 256 floats (k = K row of the job)
+            const int x0 = tile ? 256 * cb : 0;
+            const int y0 = tile ? kT * (cb ^ xt) : ((xt % kSlots) * kT + xl) * kT;
             bool quit = false;
             for (int c = 0; c < kChunks; ++c, ++Q) {
                 const uint32_t sl = Q % kRawSlots;
@@ -388,31 +393,38 @@ __global__ void __launch_bounds__(kThreads, 1)
                     quit = true;
                     break;
                 }
-                const int row = 32 * c + lane; // K row of the job
-                const bool okb =
-                    !tile || in_bounds(st, ((uint64_t)(kT * (cb ^ xt) + row) << kLog) + (uint64_t)(kT * cb + kT - 1), lim);
-                const char* src = src0 + (okb ? (uint64_t)row * pitch : 0);
-                bulk_g2s(rawb_a + sl * kRawSlotBytes + (uint32_t)lane * kRawPitch, src, 1024u, su32(&raw_full[sl]));
+                if (lane < 8) {
+                    const int x = x0 + 32 * lane, y = y0 + 32 * c;
+                    const bool okb = in_bounds(st, (uint64_t)(y + 31), tile ? (uint64_t)kN : (uint64_t)kSlots * kT * kT) &&
+                                     in_bounds(st, (uint64_t)(x + 31), tile ? 2ull * kN : 256ull);
+                    const uint32_t dst = rawb_a + sl * kRawSlotBytes + 4096u * (uint32_t)lane;
+                    if (tile)
+                        tma_2d(dst, &tmA, okb ? x : 0, okb ? y : 0, su32(&raw_full[sl]));
+                    else
+                        tma_2d(dst, &tmS, okb ? x : 0, okb ? y : 0, su32(&raw_full[sl]));
+                }
             }
             if (quit) break;
             ++J;
         }
     } else if (warp < kLoadWarps) {
         // ============================================================ loaders
-        // Warp w takes K rows 8 g + (lane & 7) of each chunk, g = w >> 1.
-        // Tile job (B operand, N = 2 xl + re/im): N groups a = 4 (ib + i) + (lane >> 3),
-        //   i = 0..3, ib = 4 (w & 1); group a is xl = 4a .. 4a + 3, whose values in
-        //   tile row m sit at columns m ^ xl = 4 (a ^ (m >> 2)) + ((m & 3) ^ j).
+        // Lane l takes K row l of each chunk (m = 32 c + l), which sits in row l of
+        // each 4 KiB box of the raw slot with its 16-byte pieces swizzled by l & 7.
+        // Tile job (B operand, N = 2 xl + re/im): N groups a = 4 w + i, i = 0..3; group
+        //   a is xl = 4a .. 4a + 3, whose values in tile row m sit at complex columns
+        //   m ^ xl = 4 A + ((m & 3) ^ j), A = a ^ (m >> 2).
         // Row job (A operand, M = real parts of zl = 0..127, then imaginary parts):
-        //   units v = ub + u, u = 0, 1, ub = 8 (w & 1) + 2 (lane >> 3); unit v is
-        //   zl = 8v .. 8v + 7 (64 contiguous raw bytes), stored as M group v (real
-        //   parts) and M group 16 + v (imaginary parts).
-        // In each 8-lane phase of a warp instruction the lanes cover 8 distinct rows,
-        // so raw reads (pitch 1040) and operand stores (128-byte core matrices) are
-        // conflict-free.
-        const int g = warp >> 1, r7 = lane & 7, ag = lane >> 3;
-        const int ib = 4 * (warp & 1), ub = 8 * (warp & 1) + 2 * ag;
-        const uint32_t pj = (uint32_t)(r7 & 3); // m & 3 for every row this thread reads
+        //   units v = 2 w + u, u = 0, 1; unit v is zl = 8v .. 8v + 7 (64 raw bytes),
+        //   stored as M group v (real parts) and M group 16 + v (imaginary parts).
+        // The 8 lanes of a read phase hold 8 consecutive rows (distinct swizzles), and
+        // the 8 lanes of a store phase fill one 128-byte core matrix: no bank conflicts.
+        const int ml = lane;
+        const uint32_t sw = (uint32_t)(ml & 7);
+        const uint32_t pj = (uint32_t)(ml & 3); // m & 3 for every row this thread reads
+        // byte offset of complex j of a tile group inside its 32-byte piece pair:
+        // piece (2 (A & 3) + (q >> 1)) ^ sw, half q & 1, q = pj ^ j
+        const uint32_t e0 = ((((pj >> 1) ^ sw) & 1u) << 4) + 8u * (pj & 1u);
         uint32_t Q = 0;
         for (uint32_t J = 0;; ++J) {
             int job = -1;
@@ -428,16 +440,17 @@ __global__ void __launch_bounds__(kThreads, 1)
                 bool tile = false;
                 int xt = 0, xl = 0;
                 if (!stop) (void)decode(job, tile, xt, xl);
-                const uint32_t rrow = rawb_a + rs * kRawSlotBytes + (uint32_t)(8 * g + r7) * kRawPitch;
+                const uint32_t rrow = rawb_a + rs * kRawSlotBytes + 128u * (uint32_t)ml;
                 uint32_t w[48];
                 if (!stop && tile) {
-                    const int mh = (32 * c + 8 * g + r7) >> 2;
+                    const int mh = (32 * c + ml) >> 2;
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
-                        const uint32_t gb = rrow + 32u * (uint32_t)((4 * (ib + i) + ag) ^ mh);
+                        const uint32_t A = (uint32_t)((4 * warp + i) ^ mh);
+                        const uint32_t gb = rrow + 4096u * (A >> 2) + (((2u * (A & 3u)) ^ (sw & 6u)) << 4);
                         float f[8];
 #pragma unroll
-                        for (int j = 0; j < 4; ++j) lds64(gb + 8u * (pj ^ (uint32_t)j), f[2 * j], f[2 * j + 1]);
+                        for (int j = 0; j < 4; ++j) lds64(gb + (e0 ^ (uint32_t)(((j >> 1) << 4) | ((j & 1) << 3))), f[2 * j], f[2 * j + 1]);
 #pragma unroll
                         for (int k = 0; k < 4; ++k)
                             split3(f[2 * k], f[2 * k + 1], w[12 * i + k], w[12 * i + 4 + k], w[12 * i + 8 + k]);
@@ -445,10 +458,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                 } else if (!stop) {
 #pragma unroll
                     for (int u = 0; u < 2; ++u) {
-                        const uint32_t vb = rrow + 64u * (uint32_t)(ub + u);
+                        const uint32_t v = (uint32_t)(2 * warp + u);
+                        const uint32_t vb = rrow + 4096u * (v >> 1);
                         float f[16]; // re0, im0, re1, im1, ...
 #pragma unroll
-                        for (int k = 0; k < 4; ++k) lds128(vb + 16u * k, f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
+                        for (int k = 0; k < 4; ++k)
+                            lds128(vb + (((4u * (v & 1u) + (uint32_t)k) ^ sw) << 4), f[4 * k], f[4 * k + 1], f[4 * k + 2],
+                                   f[4 * k + 3]);
 #pragma unroll
                         for (int k = 0; k < 4; ++k) {
                             split3(f[4 * k], f[4 * k + 2], w[24 * u + k], w[24 * u + 4 + k], w[24 * u + 8 + k]);
@@ -465,11 +481,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                     quit = true;
                     break;
                 }
-                const uint32_t slot = op_a + os * kChunkSmem + (uint32_t)g * 4096u + (uint32_t)r7 * 16u;
+                const uint32_t slot = op_a + os * kChunkSmem + (uint32_t)(ml >> 3) * 4096u + (uint32_t)(ml & 7) * 16u;
                 if (!stop && tile) {
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
-                        const uint32_t at = slot + (uint32_t)(4 * (ib + i) + ag) * 128u;
+                        const uint32_t at = slot + (uint32_t)(4 * warp + i) * 128u;
 #pragma unroll
                         for (int s = 0; s < 3; ++s)
                             sts128(at + (uint32_t)s * kSplitBytes, w[12 * i + 4 * s], w[12 * i + 4 * s + 1],
@@ -478,7 +494,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 } else if (!stop) {
 #pragma unroll
                     for (int u = 0; u < 2; ++u) {
-                        const uint32_t at = slot + (uint32_t)(ub + u) * 128u;
+                        const uint32_t at = slot + (uint32_t)(2 * warp + u) * 128u;
 #pragma unroll
                         for (int s = 0; s < 3; ++s) {
                             sts128(at + (uint32_t)s * kSplitBytes, w[24 * u + 4 * s], w[24 * u + 4 * s + 1],
@@ -731,6 +747,44 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 size_t tc14_pipe_workspace() { return 4096 + (size_t)kSlots * kT * kN * sizeof(float2); }
 
+namespace {
+
+using encode_fn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*, const cuuint64_t*,
+                               const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                               CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime.
+encode_fn tensor_map_encoder()
+{
+    static std::once_flag once;
+    static encode_fn fn = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<encode_fn>(p);
+    });
+    return fn;
+}
+
+// A float32 matrix of `rows` x `cols` (row pitch `cols` floats) read in
+// 32 x 32 boxes with the 128-byte swizzle.
+bool encode_boxes(CUtensorMap* m, const void* base, uint64_t rows, uint64_t cols)
+{
+    encode_fn enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[2] = {cols, rows};
+    const cuuint64_t strides[1] = {cols * 4};
+    const cuuint32_t box[2] = {32, 32};
+    const cuuint32_t es[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+} // namespace
+
 cudaError_t launch_tc14_pipe(const void* A, void* C, void* ws, unsigned int* st, cudaStream_t s)
 {
     static std::mutex mu;
@@ -757,8 +811,11 @@ cudaError_t launch_tc14_pipe(const void* A, void* C, void* ws, unsigned int* st,
     tab.done1 = (int*)(w + 64);
     tab.done2 = (int*)(w + 64 + 4 * kTiles);
     tab.stage = (float2*)(w + 4096);
+    CUtensorMap tmA, tmS;
+    if (!encode_boxes(&tmA, A, kN, 2 * kN) || !encode_boxes(&tmS, tab.stage, (uint64_t)kSlots * kT * kT, 2 * kT))
+        return cudaErrorInvalidValue;
     if ((e = cudaMemsetAsync(ws, 0, 4096, s)) != cudaSuccess) return e;
-    k_tc14_pipe<<<grid, kThreads, kSmemBytes, s>>>((const float2*)A, (float2*)C, tab, st);
+    k_tc14_pipe<<<grid, kThreads, kSmemBytes, s>>>(tmA, tmS, (float2*)C, tab, st);
     return cudaGetLastError();
 }
 

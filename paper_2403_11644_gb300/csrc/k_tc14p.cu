@@ -61,8 +61,9 @@
 // rounds of slack, so that a row job rarely finds its x-tile unfinished).  A
 // row job waits (bounded) until its x-tile's tile jobs are done; a tile job
 // waits (bounded) before writing its staging slot until the row jobs of the
-// x-tile that used the slot before are done (each epilogue warp counts
-// itself, so a finished x-tile pass is 128 jobs x 8 warps).  Within a CTA
+// x-tile that used the slot before are done.  A publisher warp (warp 18)
+// counts each finished job once, after one fence, so that the epilogue warps
+// never wait for their own stores to drain.  Within a CTA
 // every stage waits only on older jobs, so the earliest unfinished job can
 // always proceed.  Every wait is bounded: on time-out the kernel records
 // PTDR_ERR_TIMEOUT, each role leaves its loop, in-flight MMAs are awaited
@@ -87,7 +88,8 @@ constexpr int kLoadWarps = 8;
 constexpr int kEpiWarps = 8;
 constexpr int kMmaWarp = kLoadWarps + kEpiWarps; // 16
 constexpr int kProdWarp = kMmaWarp + 1;          // 17
-constexpr int kThreads = (kProdWarp + 1) * 32;   // 576
+constexpr int kPubWarp = kProdWarp + 1;          // 18
+constexpr int kThreads = (kPubWarp + 1) * 32;    // 608
 constexpr int kChunks = 4;                        // K chunks of 32 rows per job
 constexpr uint32_t kSplitBytes = 32u * 256u * 2u; // one split of a chunk: 32 K x 256 M/N bf16
 constexpr uint32_t kChunkSmem = 3u * kSplitBytes; // 48 KiB operand chunk
@@ -103,7 +105,7 @@ constexpr int kSlots = 4;                               // staging slots (x-tile
 constexpr int kLag = 2;                                 // row jobs of x-tile r run in round r + kLag
 constexpr int kPerRound = 2 * kT;
 constexpr int kItems = (kTiles + kLag) * kPerRound;
-constexpr int kDoneTarget = kT * kEpiWarps; // epilogue warps per finished x-tile pass
+constexpr int kDoneTarget = kT; // jobs per finished x-tile pass
 constexpr unsigned long long kWaitNs = 1000000000ull; // bound of every wait: 1 s
 constexpr uint16_t kHPos = 0x3C00u, kHNeg = 0xBC00u;  // +2^-7, -2^-7 in bf16
 
@@ -208,6 +210,21 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
            (1ull << 46);
 }
 
+__device__ __forceinline__ uint64_t pack64(uint32_t lo, uint32_t hi)
+{
+    uint64_t r;
+    asm("mov.b64 %0, {%1,%2};" : "=l"(r) : "r"(lo), "r"(hi));
+    return r;
+}
+
+// One tcgen05 product D (+)= A B with both operands in shared memory.
+__device__ __forceinline__ void mma_ss(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile("{ .reg .pred p; setp.ne.u32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(d),
+                 "l"(a), "l"(b), "r"(idesc), "r"(acc)
+                 : "memory");
+}
+
 __device__ __forceinline__ void sts128(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d)
 {
     asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
@@ -284,8 +301,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) unsigned long long raw_full[kRawSlots], raw_empty[kRawSlots], op_full[kOpSlots],
-        op_empty[kOpSlots], t_full[2], t_empty[2], bar_exit;
-    __shared__ int s_jobq[8];
+        op_empty[kOpSlots], t_full[2], t_empty[2], e_done[2], p_done[2], bar_exit;
+    __shared__ int s_jobq[8], s_pubq[4];
     __shared__ volatile int s_abort;
     __shared__ uint32_t s_tmem;
 
@@ -318,6 +335,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int i = 0; i < 2; ++i) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&t_full[i])));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&t_empty[i])), "r"(kEpiWarps));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&e_done[i])), "r"(kEpiWarps));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&p_done[i])));
         }
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bar_exit)));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -442,36 +461,41 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (!stop) (void)decode(job, tile, xt, xl);
                 const uint32_t rrow = rawb_a + rs * kRawSlotBytes + 128u * (uint32_t)ml;
                 uint32_t w[48];
+                // all 16 shared loads of the chunk first, then the splits
+                float f[32];
                 if (!stop && tile) {
                     const int mh = (32 * c + ml) >> 2;
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
                         const uint32_t A = (uint32_t)((4 * warp + i) ^ mh);
                         const uint32_t gb = rrow + 4096u * (A >> 2) + (((2u * (A & 3u)) ^ (sw & 6u)) << 4);
-                        float f[8];
 #pragma unroll
-                        for (int j = 0; j < 4; ++j) lds64(gb + (e0 ^ (uint32_t)(((j >> 1) << 4) | ((j & 1) << 3))), f[2 * j], f[2 * j + 1]);
+                        for (int j = 0; j < 4; ++j)
+                            lds64(gb + (e0 ^ (uint32_t)(((j >> 1) << 4) | ((j & 1) << 3))), f[8 * i + 2 * j], f[8 * i + 2 * j + 1]);
+                    }
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
 #pragma unroll
                         for (int k = 0; k < 4; ++k)
-                            split3(f[2 * k], f[2 * k + 1], w[12 * i + k], w[12 * i + 4 + k], w[12 * i + 8 + k]);
-                    }
+                            split3(f[8 * i + 2 * k], f[8 * i + 2 * k + 1], w[12 * i + k], w[12 * i + 4 + k], w[12 * i + 8 + k]);
                 } else if (!stop) {
 #pragma unroll
                     for (int u = 0; u < 2; ++u) {
                         const uint32_t v = (uint32_t)(2 * warp + u);
                         const uint32_t vb = rrow + 4096u * (v >> 1);
-                        float f[16]; // re0, im0, re1, im1, ...
 #pragma unroll
-                        for (int k = 0; k < 4; ++k)
-                            lds128(vb + (((4u * (v & 1u) + (uint32_t)k) ^ sw) << 4), f[4 * k], f[4 * k + 1], f[4 * k + 2],
-                                   f[4 * k + 3]);
+                        for (int k = 0; k < 4; ++k) // re0, im0, re1, im1, ...
+                            lds128(vb + (((4u * (v & 1u) + (uint32_t)k) ^ sw) << 4), f[16 * u + 4 * k], f[16 * u + 4 * k + 1],
+                                   f[16 * u + 4 * k + 2], f[16 * u + 4 * k + 3]);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 2; ++u)
 #pragma unroll
                         for (int k = 0; k < 4; ++k) {
-                            split3(f[4 * k], f[4 * k + 2], w[24 * u + k], w[24 * u + 4 + k], w[24 * u + 8 + k]);
-                            split3(f[4 * k + 1], f[4 * k + 3], w[24 * u + 12 + k], w[24 * u + 16 + k],
+                            split3(f[16 * u + 4 * k], f[16 * u + 4 * k + 2], w[24 * u + k], w[24 * u + 4 + k], w[24 * u + 8 + k]);
+                            split3(f[16 * u + 4 * k + 1], f[16 * u + 4 * k + 3], w[24 * u + 12 + k], w[24 * u + 16 + k],
                                    w[24 * u + 20 + k]);
                         }
-                    }
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(su32(&raw_empty[rs]));
@@ -560,7 +584,22 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
             job = __shfl_sync(0xffffffffu, job, 0);
-            if (job < 0) break;
+            if (warp == kLoadWarps && lane == 0) s_pubq[J & 3] = job;
+            // hand job J to the publisher warp, which must have taken job J - 2 off
+            // this barrier pair first (so that no phase of it is skipped)
+            auto hand_off = [&]() {
+                if (lane == 0) {
+                    if (J >= 2 && !mbar_wait(su32(&p_done[b]), ((J >> 1) - 1) & 1, &s_abort)) {
+                        report_status(st, PTDR_ERR_TIMEOUT);
+                        s_abort = 1;
+                    }
+                    mbar_arrive(su32(&e_done[b]));
+                }
+            };
+            if (job < 0) {
+                hand_off(); // pass the end (or abort) on to the publisher
+                break;
+            }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             bool tile = false;
             int xt = 0, idx = 0;
@@ -638,10 +677,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
             __syncwarp();
-            if (lane == 0) {
-                __threadfence();
-                atomicAdd((tile ? tab.done1 : tab.done2) + xt, 1);
-            }
+            hand_off(); // the publisher fences and counts the job's stores
         }
     } else if (warp == kMmaWarp) {
         // ============================================================ MMA issue
@@ -652,6 +688,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         // A = operand (MN-major), B = H (K-major)
         const uint32_t idesc_row =
             (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+        const uint64_t dop = sdesc(op_a, 4096u, 128u), dhh = sdesc(h_a, 128u, 2048u);
+        const uint32_t op_lo = (uint32_t)dop, op_hi = (uint32_t)(dop >> 32);
+        const uint32_t h_lo = (uint32_t)dhh, h_hi = (uint32_t)(dhh >> 32);
         bool issued = false;
         uint32_t Q = 0;
         for (uint32_t J = 0;; ++J) {
@@ -685,34 +724,30 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (c == 0) tile = __shfl_sync(0xffffffffu, tl, 0) != 0;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 if (lane == 0) {
-                    const uint32_t slot = op_a + os * kChunkSmem;
+                    // descriptors of one layout differ only in the address field (bits 0-13
+                    // of the low word): each product adds a constant to a base word
+                    const uint32_t slo = op_lo + ((os * kChunkSmem) >> 4);
+                    const uint32_t hlo = h_lo + ((uint32_t)(2 * c) * 256u >> 4);
                     const uint32_t dt = tmem + 256u * b;
+                    const uint32_t first = c ? 1u : 0u; // accumulate into the job's earlier chunks
+                    if (tile) {
 #pragma unroll
-                    for (int kk = 0; kk < 2; ++kk) {
-                        const uint64_t dh = sdesc(h_a + (uint32_t)(2 * c + kk) * 256u, 128u, 2048u);
+                        for (int kk = 0; kk < 2; ++kk)
 #pragma unroll
-                        for (int s = 0; s < 3; ++s) {
-                            const uint32_t acc = (c | kk | s) ? 1u : 0u;
-                            const uint32_t opk = slot + (uint32_t)s * kSplitBytes + (uint32_t)kk * 8192u;
-                            if (tile) {
-                                const uint64_t db = sdesc(opk, 4096u, 128u);
-                                asm volatile(
-                                    "{ .reg .pred p; setp.ne.u32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(
-                                        dt),
-                                    "l"(dh), "l"(db), "r"(idesc_tile), "r"(acc)
-                                    : "memory");
-                            } else {
+                            for (int s = 0; s < 3; ++s)
+                                mma_ss(dt, pack64(hlo + 16u * kk, h_hi),
+                                       pack64(slo + ((uint32_t)s * kSplitBytes + (uint32_t)kk * 8192u) / 16u, op_hi), idesc_tile,
+                                       (kk | s) ? 1u : first);
+                    } else {
 #pragma unroll
-                                for (int h = 0; h < 2; ++h) {
-                                    const uint64_t da = sdesc(opk + 2048u * h, 4096u, 128u);
-                                    asm volatile(
-                                        "{ .reg .pred p; setp.ne.u32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(
-                                            dt + 128u * h),
-                                        "l"(da), "l"(dh), "r"(idesc_row), "r"(acc)
-                                        : "memory");
-                                }
-                            }
-                        }
+                        for (int kk = 0; kk < 2; ++kk)
+#pragma unroll
+                            for (int s = 0; s < 3; ++s)
+#pragma unroll
+                                for (int h = 0; h < 2; ++h)
+                                    mma_ss(dt + 128u * h,
+                                           pack64(slo + ((uint32_t)s * kSplitBytes + (uint32_t)kk * 8192u + 2048u * h) / 16u, op_hi),
+                                           pack64(hlo + 16u * kk, h_hi), idesc_row, (kk | s) ? 1u : first);
                     }
                     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                                      su32(&op_empty[os]))
@@ -737,6 +772,32 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         }
         __syncwarp();
+    } else if (warp == kPubWarp) {
+        // ============================================================ publisher
+        // Once the 8 epilogue warps have stored job J (their mbarrier arrivals
+        // release the stores to this thread), one fence makes them visible at GPU
+        // scope before the job is counted for the CTAs that wait on its x-tile.
+        for (uint32_t J = 0;; ++J) {
+            const uint32_t b = J & 1;
+            int job = -1;
+            if (lane == 0) {
+                if (mbar_wait(su32(&e_done[b]), (J >> 1) & 1, &s_abort)) {
+                    job = s_pubq[J & 3];
+                } else {
+                    report_status(st, PTDR_ERR_TIMEOUT);
+                    s_abort = 1;
+                }
+                bool tl = false;
+                int xt = 0, ix = 0;
+                if (job >= 0 && decode(job, tl, xt, ix)) {
+                    __threadfence();
+                    atomicAdd((tl ? tab.done1 : tab.done2) + xt, 1);
+                }
+                mbar_arrive(su32(&p_done[b]));
+            }
+            job = __shfl_sync(0xffffffffu, job, 0);
+            if (job < 0) break;
+        }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();

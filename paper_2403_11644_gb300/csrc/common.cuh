@@ -45,6 +45,11 @@ template <typename T2> __device__ __forceinline__ T2 csub(T2 a, T2 b)
     a.y -= b.y;
     return a;
 }
+// Real rows (transforms of real data): plain scalar butterflies.
+__device__ __forceinline__ float cadd(float a, float b) { return a + b; }
+__device__ __forceinline__ float csub(float a, float b) { return a - b; }
+__device__ __forceinline__ double cadd(double a, double b) { return a + b; }
+__device__ __forceinline__ double csub(double a, double b) { return a - b; }
 
 // Multiply by (-i)^p (p taken mod 4) and by a real scale without a complex
 // multiply or a branch: an odd p swaps the real and imaginary parts, the real

@@ -51,12 +51,13 @@ __global__ void __launch_bounds__(512) k_tile(TileLaunch p, unsigned int* st)
 
 // One CTA per (mask, group of bits >= b1, chunk of 2^log_w low columns).
 // Tile element (j, w) <-> k = g 2^b1 + j 2^b0 + c0 + w; transform over j.
-template <typename T, typename OutT, Store ST>
+// V is the row value type: complex (cplx_t<T>), or T for rows of real values
+// (transforms of real band data), which only pass through buffers.
+template <typename T, typename V, typename OutT, Store ST>
 __global__ void __launch_bounds__(512) k_strided(StridedLaunch p, unsigned int* st)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    using T2 = cplx_t<T>;
-    T2* s = reinterpret_cast<T2*>(smem_raw);
+    V* s = reinterpret_cast<V*>(smem_raw);
     const int nb = p.b1 - p.b0;
     const Smem sm = make_smem(p.log_w);
     const uint64_t N = 1ull << p.n;
@@ -69,12 +70,12 @@ __global__ void __launch_bounds__(512) k_strided(StridedLaunch p, unsigned int* 
     id >>= groups_log;
     const uint64_t x = p.x_begin + id;
     const uint64_t kbase = (g << p.b1) + (chunk << p.log_w);
-    const T2* src = (const T2*)p.src + (x - p.src_row0) * N;
+    const V* src = (const V*)p.src + (x - p.src_row0) * N;
     const int E = 1 << (nb + p.log_w);
     const int wmask = (1 << p.log_w) - 1;
     for (int e = threadIdx.x; e < E; e += blockDim.x) {
         const uint64_t k = kbase + ((uint64_t)(e >> p.log_w) << p.b0) + (uint64_t)(e & wmask);
-        T2 v = mk<T>(0, 0);
+        V v{};
         if (in_bounds(st, (x - p.src_row0) * N + k, p.src_elems)) v = src[k];
         s[sm.idx(e)] = v;
     }
@@ -85,14 +86,14 @@ __global__ void __launch_bounds__(512) k_strided(StridedLaunch p, unsigned int* 
     const T scale = (T)p.scale;
     for (int e = threadIdx.x; e < E; e += blockDim.x) {
         const uint64_t k = kbase + ((uint64_t)(e >> p.log_w) << p.b0) + (uint64_t)(e & wmask);
-        const T2 v = s[sm.idx(e)];
-        if (ST == Store::RowPhaseOut) {
+        const V v = s[sm.idx(e)];
+        if constexpr (ST == Store::RowPhaseOut) {
             const uint64_t gi = (x - p.dst_row0) * N + k;
             if (in_bounds(st, gi, p.dst_elems))
                 io<OutT>::st((OutT*)p.dst + gi, phase_neg_i(v, __popcll(x & k), scale));
-        } else if (ST == Store::RowBuf) {
+        } else if constexpr (ST == Store::RowBuf) {
             const uint64_t gi = (x - p.dst_row0) * N + k;
-            if (in_bounds(st, gi, p.dst_elems)) ((T2*)p.dst)[gi] = v;
+            if (in_bounds(st, gi, p.dst_elems)) ((V*)p.dst)[gi] = v;
         } else {
             const uint64_t gi = (k ^ x) * N + k;
             if (in_bounds(st, gi, p.dst_elems)) io<OutT>::st((OutT*)p.dst + gi, v);
@@ -121,11 +122,11 @@ static cudaError_t run_tile(const TileLaunch& p, unsigned int* st, cudaStream_t 
     return cudaGetLastError();
 }
 
-template <typename T, typename OutT, Store ST>
+template <typename T, typename OutT, Store ST, typename V = cplx_t<T>>
 static cudaError_t run_strided(const StridedLaunch& p, unsigned int* st, cudaStream_t s)
 {
-    auto kern = k_strided<T, OutT, ST>;
-    const size_t bytes = smem_elems((size_t)1 << (p.b1 - p.b0), p.log_w) * sizeof(cplx_t<T>);
+    auto kern = k_strided<T, V, OutT, ST>;
+    const size_t bytes = smem_elems((size_t)1 << (p.b1 - p.b0), p.log_w) * sizeof(V);
     cudaError_t e = set_smem(kern, bytes);
     if (e != cudaSuccess) return e;
     const uint64_t blocks = p.x_count << ((p.n - p.b1) + (p.b0 - p.log_w));
@@ -178,6 +179,7 @@ template <typename T>
 static cudaError_t strided_by_store(const StridedLaunch& p, unsigned int* st, cudaStream_t s)
 {
     using T2 = cplx_t<T>;
+    if (p.real) return p.store == Store::RowBuf ? run_strided<T, T, Store::RowBuf, T>(p, st, s) : cudaErrorInvalidValue;
     switch (p.store) {
     case Store::RowBuf: return run_strided<T, T2, Store::RowBuf>(p, st, s);
     case Store::RowPhaseOut:

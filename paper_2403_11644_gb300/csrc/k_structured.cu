@@ -11,6 +11,9 @@
 // so each mask costs |T_x| transforms of length 2^{n-|x|} plus one
 // expansion pass, instead of a full length-2^n transform (the pruned X/Y
 // subtrees of Sec. IV.A; for the tridiagonal masks 2^m - 1, |T_x| = 2).
+// For a real band the rows g_t and V_t are real, so their transforms run in
+// real arithmetic (half the adds and half the bytes of complex rows); the
+// phase is applied once, in the expansion.
 #include "tile_ops.cuh"
 #include "structured.h"
 
@@ -49,13 +52,30 @@ __device__ __forceinline__ uint64_t compress_free(uint64_t z, uint64_t x, int h1
     return out;
 }
 
-// First pass: one CTA per (pair j, segment of 2^log_l values of u).
-template <typename T, typename BandT>
+// A band value as a row value: complex rows take complex or real bands,
+// real rows take real bands.
+template <typename V, typename T, typename BandT> struct band_val {
+    __device__ static __forceinline__ V ld(const BandT* p) { return io<BandT>::template ld<T>(p); }
+};
+template <typename T> struct band_val<T, T, float> {
+    __device__ static __forceinline__ T ld(const float* p) { return (T)__ldg(p); }
+};
+template <typename T> struct band_val<T, T, double> {
+    __device__ static __forceinline__ T ld(const double* p) { return (T)__ldg(p); }
+};
+
+__device__ __forceinline__ float2 as_cplx(float v) { return make_float2(v, 0.f); }
+__device__ __forceinline__ double2 as_cplx(double v) { return make_double2(v, 0.0); }
+__device__ __forceinline__ float2 as_cplx(float2 v) { return v; }
+__device__ __forceinline__ double2 as_cplx(double2 v) { return v; }
+
+// First pass: one CTA per (pair j, segment of 2^log_l values of u).  V is the
+// row value type (complex, or T for a real band).
+template <typename T, typename BandT, typename V>
 __global__ void __launch_bounds__(512) k_band_first(BandMaskLaunch p, unsigned int* st)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    using T2 = cplx_t<T>;
-    T2* s = reinterpret_cast<T2*>(smem_raw);
+    V* s = reinterpret_cast<V*>(smem_raw);
     const Smem sm = make_smem(p.log_l);
     const int segs_log = p.f - p.log_l;
     const int j = blockIdx.x >> segs_log;
@@ -70,13 +90,13 @@ __global__ void __launch_bounds__(512) k_band_first(BandMaskLaunch p, unsigned i
         const uint64_t u = (seg << p.log_l) + (uint64_t)e;
         const uint64_t k = t | expand_free(u, p.x, p.h1, p.zc);
         const uint64_t gi = (uint64_t)(d + p.s) * N + k;
-        T2 v = mk<T>(0, 0);
-        if (in_bounds(st, gi, bands_elems)) v = io<BandT>::template ld<T>(band + k);
+        V v{};
+        if (in_bounds(st, gi, bands_elems)) v = band_val<V, T, BandT>::ld(band + k);
         s[sm.idx(e)] = v;
     }
     __syncthreads();
     wht_bits(s, sm, p.log_l, 0, p.log_l);
-    T2* out = (T2*)p.ws;
+    V* out = (V*)p.ws;
     const uint64_t row = (uint64_t)j << p.f;
     for (int e = threadIdx.x; e < L; e += blockDim.x) {
         const uint64_t gi = row + (seg << p.log_l) + (uint64_t)e;
@@ -85,24 +105,23 @@ __global__ void __launch_bounds__(512) k_band_first(BandMaskLaunch p, unsigned i
 }
 
 // Expansion: C[row][z] = scale (-i)^{|x&z|} sum_j (-1)^{|z & t_j|} V_j[compress_F(z)].
-template <typename T, typename OutT>
+template <typename T, typename OutT, typename RowV>
 __global__ void __launch_bounds__(256) k_band_expand(BandMaskLaunch p, unsigned int* st)
 {
-    using T2 = cplx_t<T>;
     const uint64_t N = 1ull << p.n;
-    const T2* V = (const T2*)p.ws;
+    const RowV* V = (const RowV*)p.ws;
     const T scale = (T)p.scale;
     for (uint64_t z = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; z < N;
          z += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t v = compress_free(z, p.x, p.h1, p.zc);
-        T2 acc = mk<T>(0, 0);
+        RowV acc{};
         for (int j = 0; j < p.npairs; ++j) {
             const uint64_t gi = ((uint64_t)j << p.f) + v;
-            T2 w = mk<T>(0, 0);
+            RowV w{};
             if (in_bounds(st, gi, p.ws_elems)) w = V[gi];
             acc = (__popcll(z & p.t[j]) & 1) ? csub(acc, w) : cadd(acc, w);
         }
-        const T2 c = phase_neg_i(acc, __popcll(p.x & z), scale);
+        const cplx_t<T> c = phase_neg_i(as_cplx(acc), __popcll(p.x & z), scale);
         const uint64_t gi = p.out_row * N + z;
         if (in_bounds(st, gi, p.out_elems)) io<OutT>::st((OutT*)p.out + gi, c);
     }
@@ -115,11 +134,11 @@ static cudaError_t set_smem(K kernel, size_t bytes)
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-template <typename T, typename BandT>
+template <typename T, typename BandT, typename V>
 static cudaError_t run_first(const BandMaskLaunch& p, unsigned int* st, cudaStream_t s)
 {
-    auto kern = k_band_first<T, BandT>;
-    const size_t bytes = smem_elems(1, p.log_l) * sizeof(cplx_t<T>);
+    auto kern = k_band_first<T, BandT, V>;
+    const size_t bytes = smem_elems(1, p.log_l) * sizeof(V);
     cudaError_t e = set_smem(kern, bytes);
     if (e != cudaSuccess) return e;
     const unsigned blocks = (unsigned)p.npairs << (p.f - p.log_l);
@@ -131,10 +150,10 @@ template <typename T>
 static cudaError_t first_by_band(const BandMaskLaunch& p, unsigned int* st, cudaStream_t s)
 {
     switch (p.b_t) {
-    case PTDR_F32: return run_first<T, float>(p, st, s);
-    case PTDR_F64: return run_first<T, double>(p, st, s);
-    case PTDR_C64: return run_first<T, float2>(p, st, s);
-    case PTDR_C128: return run_first<T, double2>(p, st, s);
+    case PTDR_F32: return p.real ? run_first<T, float, T>(p, st, s) : run_first<T, float, cplx_t<T>>(p, st, s);
+    case PTDR_F64: return p.real ? run_first<T, double, T>(p, st, s) : run_first<T, double, cplx_t<T>>(p, st, s);
+    case PTDR_C64: return run_first<T, float2, cplx_t<T>>(p, st, s);
+    case PTDR_C128: return run_first<T, double2, cplx_t<T>>(p, st, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -150,7 +169,10 @@ static cudaError_t run_expand(const BandMaskLaunch& p, unsigned int* st, cudaStr
     const uint64_t N = 1ull << p.n;
     const uint64_t want = (N + 255) / 256;
     const unsigned blocks = (unsigned)(want < 152ull * 16 ? want : 152ull * 16);
-    k_band_expand<T, OutT><<<blocks, 256, 0, s>>>(p, st);
+    if (p.real)
+        k_band_expand<T, OutT, T><<<blocks, 256, 0, s>>>(p, st);
+    else
+        k_band_expand<T, OutT, cplx_t<T>><<<blocks, 256, 0, s>>>(p, st);
     return cudaGetLastError();
 }
 

@@ -74,6 +74,7 @@ struct StridedLaunch {
     uint64_t src_elems, dst_elems; // extents for the checked build's index checks
     double scale;
     int threads;
+    bool real = false; // rows of real values (intermediate buffers only: Store::RowBuf)
 };
 
 cudaError_t launch_tile(const TileLaunch& p, unsigned int* status, cudaStream_t s);

@@ -21,7 +21,8 @@ struct BandMaskLaunch {
     int npairs;   // |T_x|
     uint64_t t[kMaxBandPairs];
     int64_t d[kMaxBandPairs]; // x - 2 t: the band each pair reads
-    void* ws;     // V rows, npairs x 2^f compute-type complex values
+    bool real;    // real band: V rows hold real values
+    void* ws;     // V rows, npairs x 2^f compute-type values (complex, or real for a real band)
     uint64_t ws_elems;
     void* out;    // output array
     uint64_t out_row, out_elems;

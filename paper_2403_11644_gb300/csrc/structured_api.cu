@@ -80,7 +80,12 @@ MaskPlan plan_mask(int n, int s, uint64_t x)
     return m;
 }
 
-size_t calc_bytes(ptdr_precision p) { return p == PTDR_PREC_FP64 ? 16 : 8; }
+// Bytes of one row value: real bands are transformed as real rows.
+size_t calc_bytes(ptdr_precision p, ptdr_dtype b_t)
+{
+    const size_t c = p == PTDR_PREC_FP64 ? 16 : 8;
+    return dtype_complex(b_t) ? c : c / 2;
+}
 
 ptdr_status validate_structured(const void* bands, ptdr_dtype b_t, int n, int s,
                                 const uint64_t* h_masks, size_t n_masks, ptdr_dtype c_t,
@@ -101,12 +106,13 @@ ptdr_status validate_structured(const void* bands, ptdr_dtype b_t, int n, int s,
     return PTDR_OK;
 }
 
-size_t structured_ws(int n, int s, const uint64_t* h_masks, size_t n_masks, ptdr_precision prec)
+size_t structured_ws(int n, int s, const uint64_t* h_masks, size_t n_masks, ptdr_precision prec,
+                     ptdr_dtype b_t)
 {
     size_t mx = 0;
     for (size_t i = 0; i < n_masks; ++i) {
         MaskPlan m = plan_mask(n, s, h_masks[i]);
-        mx = std::max(mx, ((size_t)m.npairs << m.f) * calc_bytes(prec));
+        mx = std::max(mx, ((size_t)m.npairs << m.f) * calc_bytes(prec, b_t));
     }
     return mx;
 }
@@ -123,7 +129,7 @@ ptdr_status ptdr_structured_workspace_size(int n, int s, const uint64_t* h_masks
     // bands pointer not needed for sizing: pass a dummy non-null value
     ptdr_status v = validate_structured((const void*)1, b_type, n, s, h_masks, n_masks, c_type, prec);
     if (v != PTDR_OK) return v;
-    *bytes = structured_ws(n, s, h_masks, n_masks, prec);
+    *bytes = structured_ws(n, s, h_masks, n_masks, prec, b_type);
     return PTDR_OK;
 }
 
@@ -141,7 +147,7 @@ ptdr_status ptdr_decompose_structured(const void* bands, ptdr_dtype b_type, int 
     if ((uintptr_t)bands % dtype_bytes(b_type) || (uintptr_t)C % dtype_bytes(c_type))
         return PTDR_ERR_INVALID_ARG;
     if (overlaps(bands, band_bytes, C, out_bytes)) return PTDR_ERR_INVALID_ARG;
-    const size_t need = structured_ws(n, s, h_masks, n_masks, prec);
+    const size_t need = structured_ws(n, s, h_masks, n_masks, prec, b_type);
     if (need > 0 && (!workspace || workspace_bytes < need)) return PTDR_ERR_WORKSPACE;
     if (need > 0 && overlaps(workspace, need, C, out_bytes)) return PTDR_ERR_INVALID_ARG;
     if (fault_injected("plan")) return PTDR_ERR_INTERNAL;
@@ -158,7 +164,8 @@ ptdr_status ptdr_decompose_structured(const void* bands, ptdr_dtype b_type, int 
 
     cudaStream_t cs = (cudaStream_t)stream;
     const Calc calc = prec == PTDR_PREC_FP64 ? Calc::F64 : Calc::F32;
-    const size_t S = calc_bytes(prec);
+    const size_t S = calc_bytes(prec, b_type);
+    const bool real = !dtype_complex(b_type);
     int single_log = 0, tile_log = 0;
     while (((size_t)2 << single_log) * S <= kRowTileBytes) ++single_log;
     while (((size_t)2 << tile_log) * S <= kTileBytes) ++tile_log;
@@ -170,6 +177,7 @@ ptdr_status ptdr_decompose_structured(const void* bands, ptdr_dtype b_type, int 
         p.b_t = b_type;
         p.c_t = c_type;
         p.calc = calc;
+        p.real = real;
         p.n = n;
         p.s = s;
         p.x = m.x;
@@ -212,6 +220,7 @@ ptdr_status ptdr_decompose_structured(const void* bands, ptdr_dtype b_type, int 
                 sl.dst_elems = p.ws_elems;
                 sl.scale = 1.0;
                 sl.threads = 512;
+                sl.real = real;
                 e = launch_strided(sl, st, cs);
             }
         }

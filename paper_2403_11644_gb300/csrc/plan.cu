@@ -60,6 +60,13 @@ ptdr_status make_dense_plan(bool compose, int n, ptdr_dtype in_t, ptdr_dtype out
     const size_t S = p.calc == Calc::F64 ? 16 : 8;
     const size_t N = (size_t)1 << n;
     const size_t row_bytes = N * S;
+    if (compose && n == 14 && p.calc == Calc::F32 && in_t == PTDR_C64 && out_t == PTDR_C64) {
+        p.kernel = DenseKernel::Compose14;
+        p.single = true;
+        p.ws_bytes = compose14_staged_workspace();
+        *plan = p;
+        return PTDR_OK;
+    }
     if (!compose && n == 14 && p.calc == Calc::F32) {
         p.kernel = DenseKernel::Row14;
         p.single = true;
@@ -109,6 +116,20 @@ ptdr_status execute_dense(const DensePlan& p, const void* in, void* out, void* w
         if ((uintptr_t)in % 32 || (uintptr_t)out % 32 || (uintptr_t)ws % 32) return PTDR_ERR_INVALID_ARG;
         e = launch_tc14_pipe(in, out, ws, st, s);
         return e == cudaSuccess ? PTDR_OK : PTDR_ERR_CUDA;
+    }
+    if (p.kernel == DenseKernel::Compose14) {
+        // 16-byte stores of A rows; otherwise the generic tile kernels
+        if (ws && (uintptr_t)out % 16 == 0 && (uintptr_t)in % 8 == 0) {
+            e = launch_compose14_staged(in, out, scale, ws, st, s);
+            return e == cudaSuccess ? PTDR_OK : PTDR_ERR_CUDA;
+        }
+        DensePlan g = p;
+        g.kernel = DenseKernel::Tiles;
+        g.single = true;
+        g.log_l = p.n;
+        g.log_r = 0;
+        g.threads = 512;
+        return execute_dense(g, in, out, ws, scale, st, s);
     }
     if (p.kernel == DenseKernel::Row14) {
         // complex64 -> complex64 with a 16-byte aligned input takes the

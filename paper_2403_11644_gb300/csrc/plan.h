@@ -25,6 +25,7 @@ enum class DenseKernel {
     Row14,      // n = 14 FP32 decompose: staged two-pass kernel (complex64, 16-byte
                 // aligned), otherwise one CTA per mask with register rounds 5/5/4
     Tc14,       // n = 14 split-bf16 decompose, tensor-core stage over column blocks
+    Compose14,  // n = 14 FP32 compose complex64 -> complex64: staged two-pass kernel
 };
 
 struct DensePlan {
@@ -57,6 +58,9 @@ cudaError_t launch_dense14_staged(const void* A, void* C, void* ws, unsigned int
 size_t dense14_staged_workspace();
 cudaError_t launch_tc14_pipe(const void* A, void* C, void* ws, unsigned int* status, cudaStream_t s);
 size_t tc14_pipe_workspace();
+cudaError_t launch_compose14_staged(const void* C, void* A, double scale, void* ws, unsigned int* status,
+                                    cudaStream_t s);
+size_t compose14_staged_workspace();
 
 // shared helpers (ptdr_api.cu)
 ptdr_status device_ready(int* dev);

@@ -129,6 +129,35 @@ def test_compose_matches_oracle(n):
         assert rel_err(got, oracle.compose(C, scale=scale)) <= TOL["fp64"]
 
 
+def test_compose_n14_staged(a14, ref14):
+    """dense n=14 compose (complex64, FP32): the oracle's coefficients of the seeded
+    matrix are mapped back to it, and the adjoint scale 2^-14 scales it exactly."""
+    Cd = dev(ref14.astype(np.complex64))
+    B = host(ptdr.compose(Cd, precision="fp32"))
+    assert rel_err(B, a14) <= 4 * TOL["fp32"]
+    Bs = host(ptdr.compose(Cd, scale=2.0 ** -14, precision="fp32"))
+    assert rel_err(Bs * 2.0 ** 14, a14) <= 4 * TOL["fp32"]
+    assert ptdr.last_device_status() == 0
+
+
+def test_compose_n14_round_trip_and_linearity(a14):
+    Ad = dev(a14)
+    C = ptdr.decompose(Ad, precision="fp32")
+    B = host(ptdr.compose(C, precision="fp32"))
+    assert rel_err(B, a14) <= 4 * TOL["fp32"]
+    # single Pauli operators X..X (x = all ones, z = 0) and Z..Z (x = 0, z = all ones)
+    Cs = torch.zeros((1 << 14, 1 << 14), dtype=torch.complex64, device="cuda")
+    Cs[(1 << 14) - 1, 0] = 1.0
+    Cs[0, (1 << 14) - 1] = 2.0
+    P = host(ptdr.compose(Cs, precision="fp32"))
+    k = np.arange(1 << 14)
+    want_x = np.zeros_like(P)
+    want_x[k ^ ((1 << 14) - 1), k] = 1.0                      # X..X: ones on the anti-diagonal
+    want_z = np.zeros_like(P)
+    want_z[k, k] = 2.0 * (-1.0) ** np.array([bin(v).count("1") for v in k])  # 2 Z..Z: diagonal signs
+    assert np.array_equal(P, (want_x + want_z).astype(P.dtype))
+
+
 def test_compose_multipass_n15():
     rng = np.random.default_rng(15)
     A = workloads.dense_c64_direct(15, 150)

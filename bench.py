@@ -34,11 +34,16 @@ METRIC = "Pauli coeffs/s and HBM GB/s at n=14, split-BF16 TC vs FP64 plain"
 # path, from one ncu capture each (summaries under profiles/).  A figure is
 # reported only while the sources it was taken from are unchanged.
 NCU_TRAFFIC = {
-    "fp32": {"kernel": "k_dense14_staged", "bytes": 2_157_797_000 + 2_158_074_000,
+    "fp32": {"kernel": "k_dense14_staged", "bytes": 2_157_630_720 + 2_158_184_448,
              "sources": {"paper_2403_11644_gb300/csrc/k_dense14s.cu":
                          "0ca9f8674df9a8b43490c448728f48d96a7bc33a9cbd206e4409619055ad01be",
                          "paper_2403_11644_gb300/csrc/common.cuh":
-                         "f41af31f86534a7bc1c1c9a73b10f6d27e738589ae7e9bb8fe5f42eb0a9e6cc1"}},
+                         "0b8af7566a7fe16e8503406413c2ad8e3700521db352a206df357200a0645186"}},
+    "bf16x3": {"kernel": "k_tc14_pipe", "bytes": 2_283_651_328 + 2_559_128_320,
+               "sources": {"paper_2403_11644_gb300/csrc/k_tc14p.cu":
+                           "ba365f1c808331f2f0a703767f1172bcf0356d08398b996f4ae05cc4c6d14de8",
+                           "paper_2403_11644_gb300/csrc/common.cuh":
+                           "0b8af7566a7fe16e8503406413c2ad8e3700521db352a206df357200a0645186"}},
 }
 
 

@@ -227,6 +227,37 @@ ptdr_status ptdr_decompose_batched_static(const void* const* d_A, void* const* d
                                           ptdr_precision prec, void* stream);
 
 /*
+ * ptdr_decompose_host -- ptdr_decompose for matrices held in HOST memory.
+ * Defines: the same coefficients as ptdr_decompose (Sec. II.A), for `count`
+ * independent matrices; the host buffers are copied in and out by the call.
+ *
+ *   h_A       host array of `count` host pointers to the inputs (4^n elements
+ *             of a_type each, row-major); page-locked memory (cudaHostAlloc /
+ *             cudaHostRegister) lets the copies overlap, pageable memory is
+ *             accepted but its copies do not overlap.
+ *   h_C       host array of `count` host pointers to the outputs (4^n
+ *             elements of c_type each).
+ *   count     >= 1.
+ *   a_type, c_type, n, prec as for ptdr_decompose.
+ *   d_scratch device memory of at least ptdr_decompose_host_scratch_size()
+ *             bytes, 256-byte aligned: two input buffers, two output buffers
+ *             and the decomposition workspace (the library allocates nothing).
+ * The upload of matrix i + 1, the decomposition of matrix i and the download
+ * of matrix i - 1 run concurrently (two library-owned streams per device,
+ * ordered by events).  All work follows what was enqueued on `stream` before
+ * the call, and `stream` completes after the last download: synchronise it
+ * before reading h_C.  Calls from several host threads are enqueued one at a
+ * time.  Argument errors are returned before anything is enqueued.
+ */
+ptdr_status ptdr_decompose_host(const void* const* h_A, void* const* h_C, int count, ptdr_dtype a_type,
+                                ptdr_dtype c_type, int n, ptdr_precision prec, void* d_scratch,
+                                size_t d_scratch_bytes, void* stream);
+
+/* Device scratch bytes for ptdr_decompose_host.  Host only. */
+ptdr_status ptdr_decompose_host_scratch_size(int n, ptdr_dtype a_type, ptdr_dtype c_type,
+                                             ptdr_precision prec, size_t* bytes);
+
+/*
  * ptdr_last_device_status -- synchronises `stream`, returns the status word
  * the kernels wrote since the previous call (PTDR_OK if none) and clears it.
  */

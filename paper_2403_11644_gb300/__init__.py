@@ -3,8 +3,8 @@
 ``decompose(A)`` returns all 4^n coefficients c_P = 2^-n tr(P A) of a complex
 2^n x 2^n CUDA matrix; ``compose`` rebuilds A; ``decompose_structured`` handles
 diagonal/band matrices on their reachable masks; ``decompose_batched`` runs
-many matrices in one persistent launch; ``PtdrDecompose`` is the autograd
-Function.  All compute runs in libptdr's sm_103a kernels (include/ptdr.h).
+many matrices in one persistent launch; ``decompose_host`` takes host matrices
+and overlaps their transfers; ``PtdrDecompose`` is the autograd Function.  All compute runs in libptdr's sm_103a kernels (include/ptdr.h).
 """
 from .ptdr import (  # noqa: F401
     PRECISIONS,
@@ -14,7 +14,9 @@ from .ptdr import (  # noqa: F401
     decompose,
     decompose_autograd,
     decompose_batched,
+    decompose_host,
     decompose_structured,
+    host_scratch_size,
     last_device_status,
     structured_masks,
     workspace_size,

@@ -42,6 +42,8 @@ SIGNATURES = {
     "ptdr_decompose_batched": [_vp, _vp, _vp, _vp, _i, _i, _i, _i, _vp, _sz, _vp],
     "ptdr_batched_workspace_size": [_vp, _i, _i, _i, _i, _szp],
     "ptdr_decompose_batched_static": [_vp, _vp, _vp, _vp, _i, _i, _i, _i, _vp],
+    "ptdr_decompose_host": [_vp, _vp, _i, _i, _i, _i, _i, _vp, _sz, _vp],
+    "ptdr_decompose_host_scratch_size": [_i, _i, _i, _i, _szp],
     "ptdr_last_device_status": [_vp],
     "ptdr_status_string": [_i],
     "ptdr_version": [],

@@ -104,6 +104,47 @@ def compose(C: torch.Tensor, scale: float = 1.0, precision: str = "fp32", out_dt
     return A
 
 
+def host_scratch_size(n: int, a_dtype, c_dtype, precision: str) -> int:
+    """Device scratch bytes that decompose_host needs (two A, two C buffers, workspace)."""
+    out = ctypes.c_size_t(0)
+    check(_lib.load().ptdr_decompose_host_scratch_size(n, _dtype_code(a_dtype), _dtype_code(c_dtype),
+                                                       _prec(precision), ctypes.byref(out)),
+          "ptdr_decompose_host_scratch_size")
+    return out.value
+
+
+def decompose_host(As, Cs, precision: str = "fp32", device=None, scratch=None):
+    """Decomposes host (CPU) matrices As[i] into host outputs Cs[i] through the C ABI.
+
+    The call copies each matrix in, decomposes it and copies the coefficients out,
+    overlapping the transfers of neighbouring matrices; pinned tensors let the copies
+    overlap.  Returns once the work is enqueued on the current stream of `device`
+    (synchronise before reading Cs)."""
+    if len(As) != len(Cs) or not As:
+        raise ValueError("As and Cs must be non-empty lists of equal length")
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    n = _n_of(As[0].shape[0])
+    a_t, c_t = As[0].dtype, Cs[0].dtype
+    for a, c in zip(As, Cs):
+        if a.is_cuda or c.is_cuda:
+            raise ValueError("decompose_host takes host tensors")
+        if a.shape != (1 << n, 1 << n) or c.shape != (1 << n, 1 << n) or a.dtype != a_t or c.dtype != c_t:
+            raise ValueError("all matrices must have the same size and dtypes")
+        if not (a.is_contiguous() and c.is_contiguous()):
+            raise ValueError("host tensors must be contiguous")
+    need = host_scratch_size(n, a_t, c_t, precision)
+    if scratch is None:
+        scratch = torch.empty(need, dtype=torch.uint8, device=dev)
+    k = len(As)
+    ha = (ctypes.c_void_p * k)(*[a.data_ptr() for a in As])
+    hc = (ctypes.c_void_p * k)(*[c.data_ptr() for c in Cs])
+    check(_lib.load().ptdr_decompose_host(
+        ctypes.cast(ha, ctypes.c_void_p), ctypes.cast(hc, ctypes.c_void_p), k, _dtype_code(a_t), _dtype_code(c_t),
+        n, _prec(precision), ctypes.c_void_p(scratch.data_ptr()), scratch.numel(), _stream(dev)),
+        "ptdr_decompose_host")
+    return Cs
+
+
 def structured_masks(n: int, s: int) -> np.ndarray:
     """Masks reachable by a band matrix of half-width s (host computation)."""
     lib = _lib.load()

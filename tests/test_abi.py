@@ -185,6 +185,36 @@ def test_batched_argument_errors(lib):
     assert st == WORKSPACE
 
 
+def test_host_entry_point_argument_errors(lib):
+    """ptdr_decompose_host: sizes and argument checks before any device work."""
+    C64, P32 = _lib.C64, _lib.PREC_FP32
+    sz = ctypes.c_size_t(0)
+    assert lib.ptdr_decompose_host_scratch_size(10, C64, C64, P32, ctypes.byref(sz)) == OK
+    assert sz.value >= 4 * (8 << 20)  # two input and two output buffers of 2^20 complex64
+    assert lib.ptdr_decompose_host_scratch_size(16, C64, C64, P32, ctypes.byref(sz)) == INVALID
+    assert lib.ptdr_decompose_host_scratch_size(10, _lib.F32, C64, P32, ctypes.byref(sz)) == UNSUPPORTED
+    host_a = np.zeros((2, 16, 16), np.complex64)
+    host_c = np.zeros((2, 16, 16), np.complex64)
+    ha = (ctypes.c_void_p * 2)(host_a[0].ctypes.data, host_a[1].ctypes.data)
+    hc = (ctypes.c_void_p * 2)(host_c[0].ctypes.data, host_c[1].ctypes.data)
+
+    def call(a, c, count, n, scratch, nbytes, prec=P32):
+        return lib.ptdr_decompose_host(ctypes.cast(a, ctypes.c_void_p) if a is not None else None,
+                                       ctypes.cast(c, ctypes.c_void_p) if c is not None else None,
+                                       count, C64, C64, n, prec, ctypes.c_void_p(scratch), nbytes, None)
+
+    assert call(None, hc, 2, 4, FAKE_A, 1 << 20) == INVALID
+    assert call(ha, hc, 0, 4, FAKE_A, 1 << 20) == INVALID
+    assert call(ha, hc, 2, 0, FAKE_A, 1 << 20) == INVALID
+    assert call(ha, hc, 2, 4, 0, 0) == WORKSPACE
+    assert call(ha, hc, 2, 4, FAKE_A, 16) == WORKSPACE
+    assert call(ha, hc, 2, 4, FAKE_A + 64, 1 << 20) == INVALID  # scratch not 256-byte aligned
+    same = (ctypes.c_void_p * 2)(host_a[0].ctypes.data, host_a[0].ctypes.data)
+    assert call(ha, same, 2, 4, FAKE_A, 1 << 20) == INVALID  # output overlaps its input
+    if not HAVE_GPU:
+        assert call(ha, hc, 2, 4, FAKE_A, 1 << 20) == NO_DEVICE
+
+
 def test_fault_injection_plan_is_host_side():
     """PTDR_FAULT=plan makes the entry point fail on the host before any launch."""
     code = (

@@ -86,7 +86,7 @@ def _timed(fn, stream, reps=3, flush=None):
     return tot / reps
 
 
-def measure_rows(dev, stream, hbm_peak):
+def measure_rows(dev, stream, hbm_peak, only="all"):
     """Throughput of the other hot-path rows on their workloads (rank 0, N = 1).
 
     The band inputs are the seeded workloads of the GPU tests; the dense and
@@ -113,6 +113,8 @@ def measure_rows(dev, stream, hbm_peak):
         return {"bound": "fp64_alu", "achieved_ops_per_s": r, "frac": r / FP64_ADDS_PER_S}
 
     def entry(name, fn, work):
+        if only != "all" and name not in only.split(","):
+            return
         try:
             rows[name] = fn()
             rows[name].update(work(rows[name]["ms"]))
@@ -215,6 +217,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra-paths", action="store_true")
+    ap.add_argument("--rows", default="all",
+                    help="comma-separated context rows to measure (e.g. batched_512_fp32); "
+                         "given explicitly, they run even with --no-extra-paths")
     ap.add_argument("--n", type=int, default=14, help="matrix size 2^n (profiling of smaller cases)")
     return ap.parse_args()
 
@@ -495,7 +500,9 @@ def main():
             except Exception as e:  # report, never hide
                 extra[p2] = {"error": str(e)}
         result["paths"] = extra
-        result["rows"] = measure_rows(dev, stream, hbm_peak)
+        result["rows"] = measure_rows(dev, stream, hbm_peak, args.rows)
+    elif rank == 0 and args.rows != "all":
+        result["rows"] = measure_rows(dev, stream, hbm_peak, args.rows)
 
     if rank == 0 and world == 1 and N_QUBITS == 14 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline()

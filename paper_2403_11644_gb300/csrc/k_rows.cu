@@ -73,11 +73,22 @@ __global__ void __launch_bounds__(512) k_strided(StridedLaunch p, unsigned int* 
     const V* src = (const V*)p.src + (x - p.src_row0) * N;
     const int E = 1 << (nb + p.log_w);
     const int wmask = (1 << p.log_w) - 1;
-    for (int e = threadIdx.x; e < E; e += blockDim.x) {
-        const uint64_t k = kbase + ((uint64_t)(e >> p.log_w) << p.b0) + (uint64_t)(e & wmask);
-        V v{};
-        if (in_bounds(st, (x - p.src_row0) * N + k, p.src_elems)) v = src[k];
-        s[sm.idx(e)] = v;
+    for (int e0 = threadIdx.x; e0 < E; e0 += kLoadBatch * blockDim.x) {
+        V v[kLoadBatch];
+#pragma unroll
+        for (int u = 0; u < kLoadBatch; ++u) {
+            const int e = e0 + u * blockDim.x;
+            v[u] = V{};
+            if (e < E) {
+                const uint64_t k = kbase + ((uint64_t)(e >> p.log_w) << p.b0) + (uint64_t)(e & wmask);
+                if (in_bounds(st, (x - p.src_row0) * N + k, p.src_elems)) v[u] = src[k];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kLoadBatch; ++u) {
+            const int e = e0 + u * blockDim.x;
+            if (e < E) s[sm.idx(e)] = v[u];
+        }
     }
     __syncthreads();
 

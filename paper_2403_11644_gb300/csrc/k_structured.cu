@@ -86,13 +86,24 @@ __global__ void __launch_bounds__(512) k_band_first(BandMaskLaunch p, unsigned i
     const BandT* band = (const BandT*)p.bands + (uint64_t)(d + p.s) * N;
     const int L = 1 << p.log_l;
     const uint64_t bands_elems = (uint64_t)(2 * p.s + 1) * N;
-    for (int e = threadIdx.x; e < L; e += blockDim.x) {
-        const uint64_t u = (seg << p.log_l) + (uint64_t)e;
-        const uint64_t k = t | expand_free(u, p.x, p.h1, p.zc);
-        const uint64_t gi = (uint64_t)(d + p.s) * N + k;
-        V v{};
-        if (in_bounds(st, gi, bands_elems)) v = band_val<V, T, BandT>::ld(band + k);
-        s[sm.idx(e)] = v;
+    for (int e0 = threadIdx.x; e0 < L; e0 += kLoadBatch * blockDim.x) {
+        V v[kLoadBatch];
+#pragma unroll
+        for (int b = 0; b < kLoadBatch; ++b) {
+            const int e = e0 + b * blockDim.x;
+            v[b] = V{};
+            if (e < L) {
+                const uint64_t u = (seg << p.log_l) + (uint64_t)e;
+                const uint64_t k = t | expand_free(u, p.x, p.h1, p.zc);
+                const uint64_t gi = (uint64_t)(d + p.s) * N + k;
+                if (in_bounds(st, gi, bands_elems)) v[b] = band_val<V, T, BandT>::ld(band + k);
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < kLoadBatch; ++b) {
+            const int e = e0 + b * blockDim.x;
+            if (e < L) s[sm.idx(e)] = v[b];
+        }
     }
     __syncthreads();
     wht_bits(s, sm, p.log_l, 0, p.log_l);

@@ -4,6 +4,8 @@
 // (phased load, XOR-scatter) paths.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace ptdr {
@@ -84,6 +86,10 @@ __device__ void wht_bits(T2* s, const Smem& sm, int log_e, int b0, int b1)
 
 // ---------------------------------------------------------------- loads
 
+// Loads issued per thread before their values are stored to shared memory:
+// independent loads in flight hide the memory latency of the gathers.
+constexpr int kLoadBatch = 8;
+
 // d_x[k] = A[k ^ x][k] for the tile's masks x in [x0, x0 + 2^log_r) and
 // k in [k0, k0 + 2^log_l) (log_r <= log_l, both aligned).  Walked in the row
 // view: row r of A supplies the aligned block of 2^log_r columns r ^ x, so
@@ -96,15 +102,50 @@ __device__ void load_gather(cplx_t<T>* s, const Smem& sm, const InT* A, int n, u
     const uint64_t R = 1ull << log_r, L = 1ull << log_l;
     const uint64_t rb = (k0 ^ x0) & ~(L - 1);
     const int E = 1 << (log_r + log_l);
-    for (int e = threadIdx.x; e < E; e += blockDim.x) {
-        const uint64_t r = rb + ((uint64_t)e >> log_r);
-        const uint64_t c = ((r ^ x0) & ~(R - 1)) + ((uint64_t)e & (R - 1));
-        const int xl = (int)((r ^ c) - x0);
-        const int kl = (int)(c - k0);
-        const uint64_t gi = r * N + c;
-        cplx_t<T> v = mk<T>(0, 0);
-        if (in_bounds(st, gi, lim)) v = io<InT>::template ld<T>(A + gi);
-        s[sm.idx((xl << log_l) + kl)] = v;
+    if constexpr (sizeof(InT) == sizeof(cplx_t<T>) && std::is_same<InT, cplx_t<T>>::value) {
+        // same type in HBM and in the tile: asynchronous copies straight into shared
+        // memory, all of a thread's elements in flight at once (no registers held)
+        for (int e = threadIdx.x; e < E; e += blockDim.x) {
+            const uint64_t r = rb + ((uint64_t)e >> log_r);
+            const uint64_t c = ((r ^ x0) & ~(R - 1)) + ((uint64_t)e & (R - 1));
+            const int xl = (int)((r ^ c) - x0);
+            const int kl = (int)(c - k0);
+            const uint64_t gi = r * N + c;
+            cplx_t<T>* d = s + sm.idx((xl << log_l) + kl);
+            if (in_bounds(st, gi, lim)) {
+                const uint32_t da = (uint32_t)__cvta_generic_to_shared(d);
+                if constexpr (sizeof(InT) == 16)
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(da), "l"(A + gi) : "memory");
+                else
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(da), "l"(A + gi) : "memory");
+            } else {
+                *d = mk<T>(0, 0);
+            }
+        }
+        asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+        return;
+    }
+    for (int e0 = threadIdx.x; e0 < E; e0 += kLoadBatch * blockDim.x) {
+        cplx_t<T> v[kLoadBatch];
+        int dst[kLoadBatch];
+#pragma unroll
+        for (int u = 0; u < kLoadBatch; ++u) {
+            const int e = e0 + u * blockDim.x;
+            dst[u] = -1;
+            v[u] = mk<T>(0, 0);
+            if (e < E) {
+                const uint64_t r = rb + ((uint64_t)e >> log_r);
+                const uint64_t c = ((r ^ x0) & ~(R - 1)) + ((uint64_t)e & (R - 1));
+                const int xl = (int)((r ^ c) - x0);
+                const int kl = (int)(c - k0);
+                const uint64_t gi = r * N + c;
+                dst[u] = sm.idx((xl << log_l) + kl);
+                if (in_bounds(st, gi, lim)) v[u] = io<InT>::template ld<T>(A + gi);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kLoadBatch; ++u)
+            if (dst[u] >= 0) s[dst[u]] = v[u];
     }
 }
 
@@ -117,14 +158,29 @@ __device__ void load_row_phase(cplx_t<T>* s, const Smem& sm, const InT* C, int n
 {
     const uint64_t N = 1ull << n;
     const int E = 1 << (log_r + log_l);
-    for (int e = threadIdx.x; e < E; e += blockDim.x) {
-        const uint64_t x = x0 + (uint64_t)(e >> log_l);
-        const uint64_t z = k0 + (uint64_t)(e & ((1 << log_l) - 1));
-        const uint64_t gi = (x - row0) * N + z;
-        cplx_t<T> v = mk<T>(0, 0);
-        if (in_bounds(st, gi, lim)) v = io<InT>::template ld<T>(C + gi);
-        // i^p = (-i)^(4 - p)
-        s[sm.idx(e)] = phase_neg_i(v, 4 - (__popcll(x & z) & 3), scale);
+    for (int e0 = threadIdx.x; e0 < E; e0 += kLoadBatch * blockDim.x) {
+        cplx_t<T> v[kLoadBatch];
+#pragma unroll
+        for (int u = 0; u < kLoadBatch; ++u) {
+            const int e = e0 + u * blockDim.x;
+            v[u] = mk<T>(0, 0);
+            if (e < E) {
+                const uint64_t x = x0 + (uint64_t)(e >> log_l);
+                const uint64_t z = k0 + (uint64_t)(e & ((1 << log_l) - 1));
+                const uint64_t gi = (x - row0) * N + z;
+                if (in_bounds(st, gi, lim)) v[u] = io<InT>::template ld<T>(C + gi);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kLoadBatch; ++u) {
+            const int e = e0 + u * blockDim.x;
+            if (e < E) {
+                const uint64_t x = x0 + (uint64_t)(e >> log_l);
+                const uint64_t z = k0 + (uint64_t)(e & ((1 << log_l) - 1));
+                // i^p = (-i)^(4 - p)
+                s[sm.idx(e)] = phase_neg_i(v[u], 4 - (__popcll(x & z) & 3), scale);
+            }
+        }
     }
 }
 
@@ -135,12 +191,23 @@ __device__ void load_row_buf(cplx_t<T>* s, const Smem& sm, const cplx_t<T>* B, i
 {
     const uint64_t N = 1ull << n;
     const int E = 1 << (log_r + log_l);
-    for (int e = threadIdx.x; e < E; e += blockDim.x) {
-        const uint64_t x = x0 + (uint64_t)(e >> log_l);
-        const uint64_t gi = (x - row0) * N + k0 + (uint64_t)(e & ((1 << log_l) - 1));
-        cplx_t<T> v = mk<T>(0, 0);
-        if (in_bounds(st, gi, lim)) v = B[gi];
-        s[sm.idx(e)] = v;
+    for (int e0 = threadIdx.x; e0 < E; e0 += kLoadBatch * blockDim.x) {
+        cplx_t<T> v[kLoadBatch];
+#pragma unroll
+        for (int u = 0; u < kLoadBatch; ++u) {
+            const int e = e0 + u * blockDim.x;
+            v[u] = mk<T>(0, 0);
+            if (e < E) {
+                const uint64_t x = x0 + (uint64_t)(e >> log_l);
+                const uint64_t gi = (x - row0) * N + k0 + (uint64_t)(e & ((1 << log_l) - 1));
+                if (in_bounds(st, gi, lim)) v[u] = B[gi];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kLoadBatch; ++u) {
+            const int e = e0 + u * blockDim.x;
+            if (e < E) s[sm.idx(e)] = v[u];
+        }
     }
 }
 

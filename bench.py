@@ -207,6 +207,24 @@ def measure_rows(dev, stream, hbm_peak, only="all"):
     return rows
 
 
+def max_over_ranks(v: float, world: int, device) -> float:
+    """The largest value of v over the ranks (the job's time is its slowest rank's)."""
+    if world <= 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(total_ms: float, steps: int, units_per_rank: int, world: int, device):
+    """(ms per step, whole-job units/s): every rank processes units_per_rank per step
+    (weak scaling) and the job takes as long as its slowest rank."""
+    ms = max_over_ranks(total_ms, world, device) / steps
+    return ms, world * units_per_rank / (ms * 1e-3)
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -402,12 +420,7 @@ def main():
     total_ms = t0.elapsed_time(t1)
     launch_ms = [a.elapsed_time(b) for a, b in ev]
     kern_ms = float(np.mean(launch_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    ms_per_step = total_ms / args.steps
-    value = world * ncoef / (ms_per_step * 1e-3)
+    ms_per_step, value = job_throughput(total_ms, args.steps, ncoef, world, dev)
 
     in_b = A.element_size() * A.numel()
     out_b = C.element_size() * C.numel()
@@ -461,13 +474,9 @@ def main():
         ptdr.decompose_host(As, Cs, precision=prec, device=dev, scratch=scratch)
         e1.record(stream)
         torch.cuda.synchronize(dev)
-        e_ms = e0.elapsed_time(e1) / e2e_steps
-        if world > 1:
-            t = torch.tensor([e_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_ms = float(t.item())
+        e_ms, e_value = job_throughput(e0.elapsed_time(e1), e2e_steps, ncoef, world, dev)
         if rank == 0:
-            result["e2e"] = {"value": world * ncoef / (e_ms * 1e-3), "unit": "coeffs/s",
+            result["e2e"] = {"value": e_value, "unit": "coeffs/s",
                              "h2d_bytes_per_step": in_b, "d2h_bytes_per_step": out_b,
                              "ms_per_step": e_ms, "steps": e2e_steps,
                              "api": "ptdr_decompose_host (C ABI, host buffers, transfers overlapped across steps)"}

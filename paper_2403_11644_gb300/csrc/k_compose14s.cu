@@ -120,20 +120,32 @@ __global__ void __launch_bounds__(kThreads, 2)
             const int xt = r, xl = j >> 1, h = j & 1;
             if (xt >= kTiles) { __syncthreads(); continue; }
             const uint64_t x = (uint64_t)(kT * xt + xl);
-            // round a: zb bits 0-4 in registers; lanes take consecutive zl (coalesced)
+            // C[x][128 zb + 64 h + .] for every zb -> buf[zb][64] (dense 512-byte rows), by
+            // 16-byte asynchronous copies: 16 per thread in flight
+            const float2* crow = C + (x << kLog) + kH * h;
+            const uint32_t buf_a = (uint32_t)__cvta_generic_to_shared(buf);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int qc = t + kThreads * i; // 4096 pieces: row qc >> 5, pair qc & 31
+                const uint64_t gi = (x << kLog) + (uint64_t)(kT * (qc >> 5) + kH * h + 2 * (qc & 31));
+                const float2* src = crow + (size_t)kT * (qc >> 5) + 2 * (qc & 31);
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(buf_a + 16u * (uint32_t)qc),
+                             "l"(in_bounds(st, gi + 1, lim) ? src : C)
+                             : "memory");
+            }
+            asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+            __syncthreads();
+            // round a: zb bits 0-4 in registers; lanes take consecutive zl
             const int zloc = 32 * (warp & 1) + lane, q = warp >> 1;
-            const float2* crow = C + (x << kLog) + kH * h + zloc;
             float2 v[32];
 #pragma unroll
             for (int i = 0; i < 32; ++i) {
-                const uint64_t zoff = (uint64_t)kT * (32 * q + i);
-                const uint64_t z = zoff + (uint64_t)(kH * h + zloc);
-                float2 c = make_float2(0.f, 0.f);
-                if (in_bounds(st, (x << kLog) + z, lim)) c = __ldcs(crow + zoff);
+                const uint64_t z = (uint64_t)kT * (32 * q + i) + (uint64_t)(kH * h + zloc);
                 // i^p = (-i)^{(4 - p) mod 4}
-                v[i] = phase_neg_i(c, (int)((4u - (__popcll(x & z) & 3u)) & 3u), scale);
+                v[i] = phase_neg_i(buf[(32 * q + i) * kH + zloc], (int)((4u - (__popcll(x & z) & 3u)) & 3u), scale);
             }
             wht_regs<5>(v);
+            __syncthreads(); // every row of buf has been read: round a's results go back padded
 #pragma unroll
             for (int i = 0; i < 32; ++i) buf[(32 * q + i) * kRowStride + zloc] = v[i];
             // the staging slot is free once x-tile xt - kSlots has been read from it
@@ -167,11 +179,15 @@ __global__ void __launch_bounds__(kThreads, 2)
             const int R = cb ^ xt;
             // staging rows xl = 64 h + xloc, columns 128 cb .. 128 cb + 127 -> buf[xloc][zl]
             const float2* sblk = tab.stage + ((size_t)(xt % kSlots) * kT + kH * h) * kN + (size_t)kT * cb;
-#pragma unroll 4
+            const uint32_t tbuf_a = (uint32_t)__cvta_generic_to_shared(buf);
+#pragma unroll
             for (int i = 0; i < 32; ++i) {
                 const int e = t + kThreads * i; // 8192 values: row e >> 7, zl e & 127
-                buf[(e >> 7) * kTileStride + (e & 127)] = __ldcg(sblk + (size_t)(e >> 7) * kN + (e & 127));
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(tbuf_a + 8u * (uint32_t)((e >> 7) * kTileStride + (e & 127))),
+                             "l"(sblk + (size_t)(e >> 7) * kN + (e & 127))
+                             : "memory");
             }
+            asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
             __syncthreads();
             // the 64 staging rows of this block are consumed: drop their lines from L2
 #pragma unroll

@@ -39,9 +39,9 @@ NCU_TRAFFIC = {
                          "0ca9f8674df9a8b43490c448728f48d96a7bc33a9cbd206e4409619055ad01be",
                          "paper_2403_11644_gb300/csrc/common.cuh":
                          "0b8af7566a7fe16e8503406413c2ad8e3700521db352a206df357200a0645186"}},
-    "bf16x3": {"kernel": "k_tc14_pipe", "bytes": 2_283_651_328 + 2_559_128_320,
+    "bf16x3": {"kernel": "k_tc14_pipe", "bytes": 2_148_264_704 + 2_102_129_152,
                "sources": {"paper_2403_11644_gb300/csrc/k_tc14p.cu":
-                           "ba365f1c808331f2f0a703767f1172bcf0356d08398b996f4ae05cc4c6d14de8",
+                           "4e6af00cdcfa9d761b706c7fa8d5ff3947371bc37724b93ff7003df1dc99dc4f",
                            "paper_2403_11644_gb300/csrc/common.cuh":
                            "0b8af7566a7fe16e8503406413c2ad8e3700521db352a206df357200a0645186"}},
 }

@@ -173,6 +173,16 @@ __device__ __forceinline__ void mbar_arrive_tx(uint32_t bar, uint32_t bytes)
                  : "memory");
 }
 
+// Tensor-map copy of one 2-D box global -> shared with an L2 eviction policy
+// (A is read once: its lines go first, so that the staging stays in L2).
+__device__ __forceinline__ void tma_2d_hint(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar, uint64_t pol)
+{
+    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(
+                     dst),
+                 "l"(map), "r"(x), "r"(y), "r"(bar), "l"(pol)
+                 : "memory");
+}
+
 // Tensor-map copy of one 2-D box global -> shared (coordinates: x = float
 // column, y = row), completion counted on an mbarrier.
 __device__ __forceinline__ void tma_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar)
@@ -353,6 +363,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ============================================================ producer
         int next = 0;
         if (lane == 0) next = atomicAdd(tab.head, 1);
+        uint64_t evict_first;
+        asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(evict_first));
         uint32_t Q = 0, J = 0;
         for (;;) {
             int job = 0;
@@ -418,7 +430,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                                      in_bounds(st, (uint64_t)(x + 31), tile ? 2ull * kN : 256ull);
                     const uint32_t dst = rawb_a + sl * kRawSlotBytes + 4096u * (uint32_t)lane;
                     if (tile)
-                        tma_2d(dst, &tmA, okb ? x : 0, okb ? y : 0, su32(&raw_full[sl]));
+                        tma_2d_hint(dst, &tmA, okb ? x : 0, okb ? y : 0, su32(&raw_full[sl]), evict_first);
                     else
                         tma_2d(dst, &tmS, okb ? x : 0, okb ? y : 0, su32(&raw_full[sl]));
                 }

@@ -86,7 +86,7 @@ def _timed(fn, stream, reps=3, flush=None):
     return tot / reps
 
 
-def measure_rows(dev, stream, hbm_peak, only="all"):
+def measure_rows(dev, stream, hbm_peak, only="all", batched_count=512):
     """Throughput of the other hot-path rows on their workloads (rank 0, N = 1).
 
     The band inputs are the seeded workloads of the GPU tests; the dense and
@@ -157,14 +157,14 @@ def measure_rows(dev, stream, hbm_peak, only="all"):
     # a7: 512 matrices of uneven size in one persistent launch, FP32
     def batched():
         import workloads
-        ns = workloads.batched_ns(4)
+        ns = workloads.batched_ns(4)[:batched_count]
         g.manual_seed(4)
         As = [torch.randn((1 << int(n), 1 << int(n)), generator=g, device=dev, dtype=torch.complex64) for n in ns]
         Cs = [torch.empty_like(a) for a in As]
         plan = ptdr.BatchedPlan(As, Cs, "fp32")
         coeffs = int(sum(4 ** int(n) for n in ns))
         ms = _timed(plan.run, stream, flush=flush)
-        return {"workload": "512 matrices, n ~ U{4..11}, complex64 (seed 4)", "ms": ms,
+        return {"workload": f"{len(ns)} matrices, n ~ U{{4..11}}, complex64 (seed 4)", "ms": ms,
                 "coeffs_per_s": coeffs / (ms * 1e-3), "algorithmic_bytes": 16 * coeffs}
     entry("batched_512_fp32", batched, lambda ms: hbm(ms, rows["batched_512_fp32"]["algorithmic_bytes"]))
 
@@ -239,6 +239,8 @@ def parse():
                     help="comma-separated context rows to measure (e.g. batched_512_fp32); "
                          "given explicitly, they run even with --no-extra-paths")
     ap.add_argument("--n", type=int, default=14, help="matrix size 2^n (profiling of smaller cases)")
+    ap.add_argument("--batched-count", type=int, default=512,
+                    help="matrices of the batched row: the first K of the seeded 512 (profiling of smaller cases)")
     return ap.parse_args()
 
 
@@ -509,9 +511,9 @@ def main():
             except Exception as e:  # report, never hide
                 extra[p2] = {"error": str(e)}
         result["paths"] = extra
-        result["rows"] = measure_rows(dev, stream, hbm_peak, args.rows)
+        result["rows"] = measure_rows(dev, stream, hbm_peak, args.rows, args.batched_count)
     elif rank == 0 and args.rows != "all":
-        result["rows"] = measure_rows(dev, stream, hbm_peak, args.rows)
+        result["rows"] = measure_rows(dev, stream, hbm_peak, args.rows, args.batched_count)
 
     if rank == 0 and world == 1 and N_QUBITS == 14 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline()

@@ -125,12 +125,15 @@ def measure_rows(dev, stream, hbm_peak, only="all", batched_count=512):
     # Real bands are transformed in real arithmetic: the FP64 work is the pruned
     # transforms' adds plus the expansion (one add per pair and one scale per output).
     def band_fp64_ops(n, s):
+        """FP64 operations of a real band: per mask, |T_x| transforms of 2^f
+        values (f 2^f adds each), the 2^-n applied once per band value, and
+        |T_x| - 1 adds per coefficient in the expansion."""
         ops = 0
         for x in ptdr.structured_masks(n, s):
             x = int(x)
             f = n - bin(x).count("1")
             pairs = [t for t in range(x + 1) if (t & ~x) == 0 and abs(x - 2 * t) <= s] if x else [0]
-            ops += len(pairs) * f * (1 << f) + (len(pairs) + 1) * (1 << n)
+            ops += len(pairs) * (f + 1) * (1 << f) + max(len(pairs) - 1, 0) * (1 << n)
         return ops
 
     def diag():

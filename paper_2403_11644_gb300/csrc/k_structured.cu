@@ -64,13 +64,44 @@ template <typename T> struct band_val<T, T, double> {
     __device__ static __forceinline__ T ld(const double* p) { return (T)__ldg(p); }
 };
 
+// Sign flips as integer operations on the sign bit: the FP64 pipe (0.5 T
+// operations/s on this part) is kept for the adds of the transforms.
+__device__ __forceinline__ float neg_if(float a, bool c)
+{
+    return __uint_as_float(__float_as_uint(a) ^ (c ? 0x80000000u : 0u));
+}
+__device__ __forceinline__ double neg_if(double a, bool c)
+{
+    return __hiloint2double(__double2hiint(a) ^ (c ? (int)0x80000000u : 0), __double2loint(a));
+}
+__device__ __forceinline__ float2 neg_if(float2 a, bool c) { return make_float2(neg_if(a.x, c), neg_if(a.y, c)); }
+__device__ __forceinline__ double2 neg_if(double2 a, bool c) { return make_double2(neg_if(a.x, c), neg_if(a.y, c)); }
+
+// (-i)^p v for a complex v, by a swap and sign flips (no multiplies).
+template <typename T2>
+__device__ __forceinline__ T2 phase_flip(T2 v, int p)
+{
+    const bool odd = (p & 1) != 0;
+    T2 r;
+    r.x = neg_if(odd ? v.y : v.x, (p & 2) != 0);
+    r.y = neg_if(odd ? v.x : v.y, ((p ^ (p >> 1)) & 1) != 0);
+    return r;
+}
+
+__device__ __forceinline__ float scale_by(float v, float s) { return v * s; }
+__device__ __forceinline__ double scale_by(double v, double s) { return v * s; }
+__device__ __forceinline__ float2 scale_by(float2 v, float s) { return make_float2(v.x * s, v.y * s); }
+__device__ __forceinline__ double2 scale_by(double2 v, double s) { return make_double2(v.x * s, v.y * s); }
+
 __device__ __forceinline__ float2 as_cplx(float v) { return make_float2(v, 0.f); }
 __device__ __forceinline__ double2 as_cplx(double v) { return make_double2(v, 0.0); }
 __device__ __forceinline__ float2 as_cplx(float2 v) { return v; }
 __device__ __forceinline__ double2 as_cplx(double2 v) { return v; }
 
 // First pass: one CTA per (pair j, segment of 2^log_l values of u).  V is the
-// row value type (complex, or T for a real band).
+// row value type (complex, or T for a real band).  The 2^-n of the definition
+// is applied here, once per band value (exact: a power of two), instead of
+// once per coefficient in the expansion.
 template <typename T, typename BandT, typename V>
 __global__ void __launch_bounds__(512) k_band_first(BandMaskLaunch p, unsigned int* st)
 {
@@ -86,6 +117,7 @@ __global__ void __launch_bounds__(512) k_band_first(BandMaskLaunch p, unsigned i
     const BandT* band = (const BandT*)p.bands + (uint64_t)(d + p.s) * N;
     const int L = 1 << p.log_l;
     const uint64_t bands_elems = (uint64_t)(2 * p.s + 1) * N;
+    const T scale = (T)p.scale;
     for (int e0 = threadIdx.x; e0 < L; e0 += kLoadBatch * blockDim.x) {
         V v[kLoadBatch];
 #pragma unroll
@@ -96,7 +128,7 @@ __global__ void __launch_bounds__(512) k_band_first(BandMaskLaunch p, unsigned i
                 const uint64_t u = (seg << p.log_l) + (uint64_t)e;
                 const uint64_t k = t | expand_free(u, p.x, p.h1, p.zc);
                 const uint64_t gi = (uint64_t)(d + p.s) * N + k;
-                if (in_bounds(st, gi, bands_elems)) v[b] = band_val<V, T, BandT>::ld(band + k);
+                if (in_bounds(st, gi, bands_elems)) v[b] = scale_by(band_val<V, T, BandT>::ld(band + k), scale);
             }
         }
 #pragma unroll
@@ -115,13 +147,15 @@ __global__ void __launch_bounds__(512) k_band_first(BandMaskLaunch p, unsigned i
     }
 }
 
-// Expansion: C[row][z] = scale (-i)^{|x&z|} sum_j (-1)^{|z & t_j|} V_j[compress_F(z)].
+// Expansion: C[row][z] = (-i)^{|x&z|} sum_j (-1)^{|z & t_j|} V_j[compress_F(z)]
+// (V already carries the 2^-n).  The sum starts from the signed first term, so
+// a mask of |T_x| pairs costs |T_x| - 1 adds per coefficient; signs and the
+// phase are sign-bit flips and a swap.
 template <typename T, typename OutT, typename RowV>
 __global__ void __launch_bounds__(256) k_band_expand(BandMaskLaunch p, unsigned int* st)
 {
     const uint64_t N = 1ull << p.n;
     const RowV* V = (const RowV*)p.ws;
-    const T scale = (T)p.scale;
     for (uint64_t z = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; z < N;
          z += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t v = compress_free(z, p.x, p.h1, p.zc);
@@ -130,9 +164,11 @@ __global__ void __launch_bounds__(256) k_band_expand(BandMaskLaunch p, unsigned 
             const uint64_t gi = ((uint64_t)j << p.f) + v;
             RowV w{};
             if (in_bounds(st, gi, p.ws_elems)) w = V[gi];
-            acc = (__popcll(z & p.t[j]) & 1) ? csub(acc, w) : cadd(acc, w);
+            const bool neg = (__popcll(z & p.t[j]) & 1) != 0;
+            if (j == 0) acc = neg_if(w, neg);
+            else acc = neg ? csub(acc, w) : cadd(acc, w);
         }
-        const cplx_t<T> c = phase_neg_i(as_cplx(acc), __popcll(p.x & z), scale);
+        const cplx_t<T> c = phase_flip(as_cplx(acc), __popcll(p.x & z));
         const uint64_t gi = p.out_row * N + z;
         if (in_bounds(st, gi, p.out_elems)) io<OutT>::st((OutT*)p.out + gi, c);
     }

@@ -38,7 +38,9 @@ ptdr_status ptdr_structured_masks(int n, int s, uint64_t* h_masks, size_t* count
 
 // ---------------------------------------------------------------- planning
 
+#include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "structured.h"
@@ -106,16 +108,89 @@ ptdr_status validate_structured(const void* bands, ptdr_dtype b_t, int n, int s,
     return PTDR_OK;
 }
 
+// The masks are independent: each is a chain first pass -> strided passes ->
+// expansion through its own V rows.  Run on one stream, the chains of the
+// many short masks (a few CTAs each: FP64 work on a few SMs runs at a few
+// 1/152 of the GPU's FP64 rate) leave the GPU idle, so the masks are dealt
+// to up to kChains chains, longest first to the least loaded (work =
+// transform and expansion values), each chain on a library stream with its
+// own V region.  The plan depends only on the mask list, so the workspace
+// query and the call agree.
+constexpr int kChains = 4;
+
+struct ChainPlan {
+    std::vector<int> chain;      // chain of each mask
+    size_t region[kChains] = {}; // V bytes of each chain (its largest mask), 256-aligned
+    int chains = 0;
+    size_t total = 0;
+};
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+ChainPlan plan_chains(int n, int s, const uint64_t* h_masks, size_t n_masks, ptdr_precision prec,
+                      ptdr_dtype b_t)
+{
+    ChainPlan cp;
+    cp.chain.assign(n_masks, 0);
+    cp.chains = (int)std::min<size_t>(n_masks, kChains);
+    std::vector<std::pair<double, size_t>> order(n_masks);
+    std::vector<size_t> vbytes(n_masks);
+    for (size_t i = 0; i < n_masks; ++i) {
+        const MaskPlan m = plan_mask(n, s, h_masks[i]);
+        vbytes[i] = ((size_t)m.npairs << m.f) * calc_bytes(prec, b_t);
+        const double work = (double)m.npairs * (m.f + 1) * std::ldexp(1.0, m.f) + std::ldexp(1.0, n);
+        order[i] = {work, i};
+    }
+    std::stable_sort(order.begin(), order.end(),
+                     [](const std::pair<double, size_t>& a, const std::pair<double, size_t>& b) {
+                         return a.first > b.first;
+                     });
+    double load[kChains] = {};
+    for (const auto& wi : order) {
+        int c = 0;
+        for (int k = 1; k < cp.chains; ++k)
+            if (load[k] < load[c]) c = k;
+        load[c] += wi.first;
+        cp.chain[wi.second] = c;
+        cp.region[c] = std::max(cp.region[c], align256(vbytes[wi.second]));
+    }
+    for (int c = 0; c < cp.chains; ++c) cp.total += cp.region[c];
+    return cp;
+}
+
 size_t structured_ws(int n, int s, const uint64_t* h_masks, size_t n_masks, ptdr_precision prec,
                      ptdr_dtype b_t)
 {
-    size_t mx = 0;
-    for (size_t i = 0; i < n_masks; ++i) {
-        MaskPlan m = plan_mask(n, s, h_masks[i]);
-        mx = std::max(mx, ((size_t)m.npairs << m.f) * calc_bytes(prec, b_t));
-    }
-    return mx;
+    return plan_chains(n, s, h_masks, n_masks, prec, b_t).total;
 }
+
+// Library streams of the chains, one set per device, created on first use.
+struct ChainStreams {
+    bool ready = false;
+    cudaStream_t s[kChains] = {};
+    cudaEvent_t fork = nullptr, join[kChains] = {};
+};
+std::mutex g_chain_mu; // also serialises the enqueue of concurrent calls
+ChainStreams g_chain[128];
+
+ptdr_status chain_streams(int dev, ChainStreams** out)
+{
+    ChainStreams& c = g_chain[dev];
+    if (!c.ready) {
+        bool ok = cudaEventCreateWithFlags(&c.fork, cudaEventDisableTiming) == cudaSuccess;
+        for (int k = 0; k < kChains && ok; ++k)
+            ok = cudaStreamCreateWithFlags(&c.s[k], cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&c.join[k], cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            return PTDR_ERR_CUDA;
+        }
+        c.ready = true;
+    }
+    *out = &c;
+    return PTDR_OK;
+}
+
 
 } // namespace
 
@@ -163,6 +238,20 @@ ptdr_status ptdr_decompose_structured(const void* bands, ptdr_dtype b_type, int 
     if (fault_injected("launch")) return PTDR_ERR_CUDA;
 
     cudaStream_t cs = (cudaStream_t)stream;
+    const ChainPlan cp = plan_chains(n, s, h_masks, n_masks, prec, b_type);
+    size_t region_off[kChains] = {};
+    for (int c = 1; c < cp.chains; ++c) region_off[c] = region_off[c - 1] + cp.region[c - 1];
+    std::unique_lock<std::mutex> lk(g_chain_mu, std::defer_lock);
+    ChainStreams* chs = nullptr;
+    if (cp.chains > 1) {
+        lk.lock();
+        v = chain_streams(dev, &chs);
+        if (v != PTDR_OK) return v;
+        // the chains follow whatever the caller enqueued on its stream before
+        if (cudaEventRecord(chs->fork, cs) != cudaSuccess) return PTDR_ERR_CUDA;
+        for (int c = 0; c < cp.chains; ++c)
+            if (cudaStreamWaitEvent(chs->s[c], chs->fork, 0) != cudaSuccess) return PTDR_ERR_CUDA;
+    }
     const Calc calc = prec == PTDR_PREC_FP64 ? Calc::F64 : Calc::F32;
     const size_t S = calc_bytes(prec, b_type);
     const bool real = !dtype_complex(b_type);
@@ -172,6 +261,9 @@ ptdr_status ptdr_decompose_structured(const void* bands, ptdr_dtype b_type, int 
     cudaError_t e = cudaSuccess;
     for (size_t i = 0; i < n_masks && e == cudaSuccess; ++i) {
         MaskPlan m = plan_mask(n, s, h_masks[i]);
+        const int c = cp.chain[i];
+        cudaStream_t ms = cp.chains > 1 ? chs->s[c] : cs;
+        void* vws = workspace ? (void*)((char*)workspace + region_off[c]) : nullptr;
         BandMaskLaunch p{};
         p.bands = bands;
         p.b_t = b_type;
@@ -189,7 +281,7 @@ ptdr_status ptdr_decompose_structured(const void* bands, ptdr_dtype b_type, int 
             p.t[j] = m.t[j];
             p.d[j] = m.d[j];
         }
-        p.ws = workspace;
+        p.ws = vws;
         p.ws_elems = (uint64_t)m.npairs << m.f;
         p.out = C;
         p.out_row = i;
@@ -199,13 +291,13 @@ ptdr_status ptdr_decompose_structured(const void* bands, ptdr_dtype b_type, int 
         p.log_l = single ? m.f : tile_log;
         p.threads = ((size_t)1 << p.log_l) * S >= 32 * 1024 ? 512 : 256;
         // A mask the band cannot reach has no pairs: its row is written as zeros.
-        if (m.npairs > 0) e = launch_band_first(p, st, cs);
+        if (m.npairs > 0) e = launch_band_first(p, st, ms);
         if (e == cudaSuccess && m.npairs > 0 && !single) {
             std::vector<StridedPass> passes = strided_schedule(p.log_l, m.f, S);
             for (size_t q = 0; q < passes.size() && e == cudaSuccess; ++q) {
                 StridedLaunch sl{};
-                sl.src = workspace;
-                sl.dst = workspace;
+                sl.src = vws;
+                sl.dst = vws;
                 sl.calc = calc;
                 sl.store = Store::RowBuf;
                 sl.n = m.f;
@@ -221,11 +313,19 @@ ptdr_status ptdr_decompose_structured(const void* bands, ptdr_dtype b_type, int 
                 sl.scale = 1.0;
                 sl.threads = 512;
                 sl.real = real;
-                e = launch_strided(sl, st, cs);
+                e = launch_strided(sl, st, ms);
             }
         }
-        if (e == cudaSuccess) e = launch_band_expand(p, st, cs);
+        if (e == cudaSuccess) e = launch_band_expand(p, st, ms);
     }
+    // the caller's stream completes after every chain (also after an error:
+    // the joins keep the library streams ordered for the next call)
+    if (cp.chains > 1)
+        for (int c = 0; c < cp.chains; ++c) {
+            const bool ok = cudaEventRecord(chs->join[c], chs->s[c]) == cudaSuccess &&
+                            cudaStreamWaitEvent(cs, chs->join[c], 0) == cudaSuccess;
+            if (!ok && e == cudaSuccess) e = cudaErrorUnknown;
+        }
     return e == cudaSuccess ? PTDR_OK : PTDR_ERR_CUDA;
 }
 

@@ -231,3 +231,27 @@ def test_python_api_rejects_cpu_tensors():
     from paper_2403_11644_gb300 import decompose as dec
     with pytest.raises(ValueError, match="CUDA"):
         dec(torch.zeros(4, 4, dtype=torch.complex64))
+
+
+def test_structured_workspace_covers_concurrent_masks(lib):
+    """The band masks run as independent chains on up to four streams, each
+    chain with its own V region: one mask needs exactly its V rows; many
+    masks need at least the largest V and at most every V (256-aligned)."""
+    def ws(n, s, masks, b_t, prec):
+        arr = np.asarray(masks, np.uint64)
+        out = ctypes.c_size_t(0)
+        st = lib.ptdr_structured_workspace_size(n, s, arr.ctypes.data_as(ctypes.c_void_p), len(arr), b_t,
+                                                b_t, prec, ctypes.byref(out))
+        return st, out.value
+
+    def vbytes(n, s, x, elem):
+        pairs = [t for t in range(x + 1) if (t & ~x) == 0 and abs(x - 2 * t) <= s] if x else [0]
+        return len(pairs) * (1 << (n - bin(x).count("1"))) * elem
+
+    assert ws(26, 0, [0], _lib.F64, _lib.PREC_FP64) == (OK, 8 << 26)
+    masks = [int(m) for m in oracle.band_masks(22, 1)]
+    st, b = ws(22, 1, masks, _lib.F64, _lib.PREC_FP64)
+    each = [vbytes(22, 1, x, 8) for x in masks]
+    assert st == OK and max(each) < b <= sum((v + 255) // 256 * 256 for v in each)
+    st, b = ws(10, 3, [int(m) for m in oracle.band_masks(10, 3)], _lib.C128, _lib.PREC_FP64)
+    assert st == OK and b > 0

@@ -85,8 +85,12 @@ ptdr_status make_dense_plan(bool compose, int n, ptdr_dtype in_t, ptdr_dtype out
         p.threads = tile >= 32 * 1024 ? 512 : 256;
     } else {
         p.single = false;
-        p.log_r = 0;
-        p.log_l = ilog2(kTileBytes / S);
+        // Decompose: 4 masks per first-pass tile, so that each row of A
+        // supplies a 4-value piece (a whole 32-byte sector of complex64)
+        // instead of one value per sector; A is far larger than L2 here, so
+        // the rest of a sector is not there when its own mask is gathered.
+        p.log_r = compose ? 0 : 2;
+        p.log_l = ilog2(kTileBytes / S) - p.log_r;
         p.threads = 512;
         p.passes = strided_schedule(p.log_l, n, S);
         // Decompose can keep the intermediate in C when C has the compute
@@ -100,6 +104,11 @@ ptdr_status make_dense_plan(bool compose, int n, ptdr_dtype in_t, ptdr_dtype out
         } else {
             p.chunk = std::max<size_t>(1, std::min<size_t>(N, kChunkBytes / row_bytes));
             p.ws_bytes = p.chunk * row_bytes;
+        }
+        if (p.chunk % ((size_t)1 << p.log_r)) { // a chunk holds whole tiles of masks
+            p.log_l += p.log_r;
+            p.log_r = 0;
+            p.passes = strided_schedule(p.log_l, n, S);
         }
     }
     *plan = p;
@@ -176,7 +185,7 @@ ptdr_status execute_dense(const DensePlan& p, const void* in, void* out, void* w
         t.load = p.compose ? Load::RowPhaseC : Load::GatherA;
         t.store = Store::RowBuf;
         t.n = p.n;
-        t.log_r = 0;
+        t.log_r = p.log_r;
         t.log_l = p.log_l;
         t.x_begin = x0;
         t.x_count = p.chunk;

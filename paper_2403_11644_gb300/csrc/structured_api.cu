@@ -116,7 +116,7 @@ ptdr_status validate_structured(const void* bands, ptdr_dtype b_t, int n, int s,
 // transform and expansion values), each chain on a library stream with its
 // own V region.  The plan depends only on the mask list, so the workspace
 // query and the call agree.
-constexpr int kChains = 4;
+constexpr int kChains = 8;
 
 struct ChainPlan {
     std::vector<int> chain;      // chain of each mask

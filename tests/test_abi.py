@@ -234,7 +234,7 @@ def test_python_api_rejects_cpu_tensors():
 
 
 def test_structured_workspace_covers_concurrent_masks(lib):
-    """The band masks run as independent chains on up to four streams, each
+    """The band masks run as independent chains on up to eight streams, each
     chain with its own V region: one mask needs exactly its V rows; many
     masks need at least the largest V and at most every V (256-aligned)."""
     def ws(n, s, masks, b_t, prec):

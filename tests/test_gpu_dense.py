@@ -104,7 +104,7 @@ def test_n14_fp64_into_c64_workspace_path(a14, ref14):
 def test_n15_fp32_multipass():
     A = workloads.dense_c64_direct(15, 15)
     C = host(ptdr.decompose(dev(A), precision="fp32"))
-    xs = workloads.sample_masks(15, 15, count=6)
+    xs = workloads.sample_masks(15, 15, count=16)
     ref = oracle.fwht(A, xs=xs)
     assert rel_err(C[xs.astype(np.int64)], ref) <= TOL["fp32"]
 

@@ -228,6 +228,29 @@ def job_throughput(total_ms: float, steps: int, units_per_rank: int, world: int,
     return ms, world * units_per_rank / (ms * 1e-3)
 
 
+def host_link_gbs(h_in, h_out, d_in, d_out, dev, reps=3):
+    """GB/s each way of plain copies host -> device and device -> host run at
+    the same time on two streams: the bound of the host-buffer path, whose
+    every step moves its input in and its output out."""
+    import torch
+    up, down = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+
+    def both():
+        with torch.cuda.stream(up):
+            d_in.copy_(h_in, non_blocking=True)
+        with torch.cuda.stream(down):
+            h_out.copy_(d_out, non_blocking=True)
+
+    both()
+    torch.cuda.synchronize(dev)
+    t = time.perf_counter()
+    for _ in range(reps):
+        both()
+    torch.cuda.synchronize(dev)
+    sec = time.perf_counter() - t
+    return reps * min(h_in.numel() * h_in.element_size(), h_out.numel() * h_out.element_size()) / sec / 1e9
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -465,6 +488,8 @@ def main():
     if not args.no_e2e:
         A_pin = torch.from_numpy(A_h).pin_memory()
         C_pins = [torch.empty(C.shape, dtype=C.dtype).pin_memory() for _ in range(2)]
+        # the host link this process sees (A is rewritten with its own values)
+        link = host_link_gbs(A_pin, C_pins[0], A, C, dev)
         e2e_steps = max(3, min(args.steps, 8))
         scratch = torch.empty(ptdr.host_scratch_size(N_QUBITS, A.dtype, out_dtype, prec), dtype=torch.uint8,
                               device=dev)
@@ -484,6 +509,8 @@ def main():
             result["e2e"] = {"value": e_value, "unit": "coeffs/s",
                              "h2d_bytes_per_step": in_b, "d2h_bytes_per_step": out_b,
                              "ms_per_step": e_ms, "steps": e2e_steps,
+                             "link_gbs_each_way": link,
+                             "link_bound_ms_per_step": max(in_b, out_b) / (link * 1e9) * 1e3,
                              "api": "ptdr_decompose_host (C ABI, host buffers, transfers overlapped across steps)"}
         del scratch
 

@@ -83,6 +83,9 @@ ptdr_status make_dense_plan(bool compose, int n, ptdr_dtype in_t, ptdr_dtype out
         p.log_r = lr;
         const size_t tile = row_bytes << lr;
         p.threads = tile >= 32 * 1024 ? 512 : 256;
+        // the generic fields above remain the fallback for misaligned buffers
+        if (!compose && p.calc == Calc::F32 && out_t == PTDR_C64 && in_t == PTDR_C64 && n >= 9 && n <= 12)
+            p.kernel = DenseKernel::Rr;
     } else {
         p.single = false;
         // Decompose: 4 masks per first-pass tile, so that each row of A
@@ -138,6 +141,16 @@ ptdr_status execute_dense(const DensePlan& p, const void* in, void* out, void* w
         g.log_l = p.n;
         g.log_r = 0;
         g.threads = 512;
+        return execute_dense(g, in, out, ws, scale, st, s);
+    }
+    if (p.kernel == DenseKernel::Rr) {
+        // 16-byte piece copies and 16-byte stores; otherwise the generic tile kernel
+        if ((uintptr_t)in % 16 == 0 && (uintptr_t)out % 16 == 0) {
+            e = launch_rr_dense(p.n, in, out, scale, st, s);
+            return e == cudaSuccess ? PTDR_OK : PTDR_ERR_CUDA;
+        }
+        DensePlan g = p;
+        g.kernel = DenseKernel::Tiles;
         return execute_dense(g, in, out, ws, scale, st, s);
     }
     if (p.kernel == DenseKernel::Row14) {

@@ -26,6 +26,8 @@ enum class DenseKernel {
                 // aligned), otherwise one CTA per mask with register rounds 5/5/4
     Tc14,       // n = 14 split-bf16 decompose, tensor-core stage over column blocks
     Compose14,  // n = 14 FP32 compose complex64 -> complex64: staged two-pass kernel
+    Rr,         // n = 9 .. 12 FP32 decompose complex64 -> complex64 (16-byte aligned):
+                // register-round items, one CTA per 2^(13-n) masks; otherwise the generic tiles
 };
 
 struct DensePlan {
@@ -61,6 +63,7 @@ size_t tc14_pipe_workspace();
 cudaError_t launch_compose14_staged(const void* C, void* A, double scale, void* ws, unsigned int* status,
                                     cudaStream_t s);
 size_t compose14_staged_workspace();
+cudaError_t launch_rr_dense(int n, const void* A, void* C, double scale, unsigned int* status, cudaStream_t s);
 
 // shared helpers (ptdr_api.cu)
 ptdr_status device_ready(int* dev);

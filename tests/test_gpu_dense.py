@@ -45,7 +45,7 @@ def test_workload_dense_n6(hermitian):
 
 @pytest.mark.parametrize("hermitian", [False, True])
 @pytest.mark.parametrize("prec,adt", [("fp64", np.complex128), ("fp32", np.complex64),
-                                      ("fp64", np.complex64)])
+                                      ("fp64", np.complex64), ("fp32", np.complex128)])
 def test_workload_dense_n12(hermitian, prec, adt):
     """dense n=12, complex128/complex64, general/Hermitian, FP64 and FP32 paths."""
     A = workloads.dense(12, 112 if hermitian else 12, dtype=adt, hermitian=hermitian)

@@ -4,9 +4,9 @@
 // items are (matrix, block of masks) pairs taken from an atomic queue in
 // longest-first order, so a single grid of resident CTAs balances matrices
 // of n = 1..13 without a launch per matrix.  Items of complex64 matrices of
-// n = 9, 10, 11 computed in FP32 run a register-round path (below); every
-// other item runs the generic tile path (gather, shared-memory passes,
-// phased write-out).
+// n = 9, 10, 11 computed in FP32 run the register-round items of
+// rr_items.cuh; every other item runs the generic tile path (gather,
+// shared-memory passes, phased write-out).
 #include <algorithm>
 #include <type_traits>
 

@@ -490,7 +490,7 @@ def main():
         C_pins = [torch.empty(C.shape, dtype=C.dtype).pin_memory() for _ in range(2)]
         # the host link this process sees (A is rewritten with its own values)
         link = host_link_gbs(A_pin, C_pins[0], A, C, dev)
-        e2e_steps = max(3, min(args.steps, 8))
+        e2e_steps = max(3, min(args.steps, 20))  # the first upload and the last download are not overlapped
         scratch = torch.empty(ptdr.host_scratch_size(N_QUBITS, A.dtype, out_dtype, prec), dtype=torch.uint8,
                               device=dev)
         As = [A_pin] * e2e_steps

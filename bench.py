@@ -63,9 +63,35 @@ def ncu_traffic(prec, n):
     return e["kernel"], e["bytes"]
 
 
-# FP64 add throughput of one GB300 (adds/s), measured with an add-chain
-# microbenchmark: the bound of the FP64 transforms.
-FP64_ADDS_PER_S = 0.505e12
+# Relative max-abs error bounds against the FP64 oracle, per arithmetic path.
+TOLERANCE = {"fp64": 1e-12, "fp32": 1e-5, "bf16x3": 2e-6, "fixed": 1e-12}
+
+
+def fp64_add_rate(dev, stream, reps=3):
+    """FP64 adds/s of this GPU, measured now with the library's add-chain probe
+    (8 independent chains per thread, 8 CTAs of 256 threads per SM): the bound
+    of the FP64 transforms."""
+    import ctypes
+    import torch
+    from paper_2403_11644_gb300 import _lib
+    lib = _lib.load()
+    blocks = torch.cuda.get_device_properties(dev).multi_processor_count * 8
+    sink = torch.zeros(blocks, dtype=torch.float64, device=dev)
+    adds = ctypes.c_double(0)
+    sp = ctypes.c_void_p(stream.cuda_stream)
+
+    def run():
+        _lib.check(lib.ptdr_probe_fp64_adds(ctypes.c_void_p(sink.data_ptr()), blocks, 256, 4096,
+                                            ctypes.byref(adds), sp), "ptdr_probe_fp64_adds")
+    run()
+    torch.cuda.synchronize(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        run()
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    return reps * adds.value / (a.elapsed_time(b) * 1e-3)
 
 
 def _timed(fn, stream, reps=3, flush=None):
@@ -86,7 +112,7 @@ def _timed(fn, stream, reps=3, flush=None):
     return tot / reps
 
 
-def measure_rows(dev, stream, hbm_peak, only="all", batched_count=512):
+def measure_rows(dev, stream, hbm_peak, fp64_rate, only="all", batched_count=512):
     """Throughput of the other hot-path rows on their workloads (rank 0, N = 1).
 
     The band inputs are the seeded workloads of the GPU tests; the dense and
@@ -110,7 +136,7 @@ def measure_rows(dev, stream, hbm_peak, only="all", batched_count=512):
 
     def fp64(ms, adds):
         r = adds / (ms * 1e-3)
-        return {"bound": "fp64_alu", "achieved_ops_per_s": r, "frac": r / FP64_ADDS_PER_S}
+        return {"bound": "fp64_alu", "achieved_ops_per_s": r, "frac": r / fp64_rate}
 
     def entry(name, fn, work):
         if only != "all" and name not in only.split(","):
@@ -257,7 +283,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default=None, help="fp32 | fp64 | bf16x3 | fp16x2")
+    ap.add_argument("--precision", default=None, help="fp32 | fp64 | bf16x3 | fixed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra-paths", action="store_true")
@@ -336,18 +362,31 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_baseline(seconds=12.0):
-    """The oracle's tree walk (Algorithms 1-4, forest split) on a bounded sample of the
-    n=14 workload: whole subtrees of the forest cut at level 9 (1,024 coefficients each,
-    every coefficient an O(2^14) trace), one subtree per core per round, as many rounds
-    as fit the time budget."""
-    import oracle
-    import workloads
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith(("model name", "cpu model")):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
 
-    A = workloads.dense_c64_direct(N_QUBITS, SEED).astype(np.complex128)
-    threads = oracle.max_threads()
-    cut = 9
-    per_tree = 4 ** (N_QUBITS - cut)
+
+def _tree_rate(A, threads, seconds, cut=9):
+    """Coefficients/s of the oracle's tree walk (Algorithms 1-4) over whole subtrees of
+    the forest cut at level `cut`, `threads` subtrees per round, for about `seconds`."""
+    import oracle
+    n = A.shape[0].bit_length() - 1
+    per_tree = 4 ** (n - cut)
     done, t0, nxt = 0, time.perf_counter(), 0
     while True:
         oracle.tree(A, cut=cut, subtrees=(nxt, nxt + threads), threads=threads)
@@ -356,9 +395,71 @@ def cpu_baseline(seconds=12.0):
         el = time.perf_counter() - t0
         if el >= seconds or nxt >= 4 ** cut:
             break
-    return {"value": done * per_tree / el, "unit": "coeffs/s", "cores": threads, "kind": "oracle",
-            "sample": f"{done} of {4 ** cut} subtrees (cut at level {cut}) of the n=14 tree walk, "
-                      f"{done * per_tree} coefficients in {el:.1f} s"}
+    return done * per_tree / el, done, el
+
+
+def _direct_rate(A, threads, seconds):
+    """Coefficients/s of the oracle's direct sparse trace (Sec. II.A) over whole mask
+    rows (2^n coefficients each), `threads` masks per round, for about `seconds`."""
+    import oracle
+    N = A.shape[0]
+    done, t0, nxt = 0, time.perf_counter(), 1
+    while True:
+        xs = (np.arange(nxt, nxt + threads) % N).astype(np.uint64)
+        oracle.direct(A, xs=xs, threads=threads)
+        nxt += threads
+        done += threads
+        el = time.perf_counter() - t0
+        if el >= seconds or done >= N:
+            break
+    return done * N / el, done, el
+
+
+def cpu_baseline(seconds=12.0):
+    """The oracle on the host cores, on bounded samples of the n=14 workload.
+
+    The headline value is the tree walk (Algorithms 1-4, forest split) on all
+    cores; beside it, the same walk on one core, the direct sparse trace on all
+    cores and on one core, and (labelled extra) the textbook FWHT check over the
+    whole matrix."""
+    import oracle
+    import workloads
+
+    A = workloads.dense_c64_direct(N_QUBITS, SEED).astype(np.complex128)
+    threads = oracle.max_threads()
+    v, done, el = _tree_rate(A, threads, seconds)
+    v1, done1, el1 = _tree_rate(A, 1, seconds / 4)
+    dv, ddone, del_ = _direct_rate(A, threads, seconds / 3)
+    dv1, ddone1, del1 = _direct_rate(A, 1, seconds / 4)
+    t0 = time.perf_counter()
+    oracle.fwht(A, threads=threads)
+    fw = time.perf_counter() - t0
+    return {"value": v, "unit": "coeffs/s", "cores": threads, "kind": "oracle", "cpu_model": cpu_model(),
+            "sample": f"{done} of {4 ** 9} subtrees (cut at level 9) of the n=14 tree walk, "
+                      f"{done * 4 ** (N_QUBITS - 9)} coefficients in {el:.1f} s on {threads} threads",
+            "modes": {
+                "tree_all_cores": {"coeffs_per_s": v, "threads": threads, "seconds": el, "subtrees": done},
+                "tree_1_core": {"coeffs_per_s": v1, "threads": 1, "seconds": el1, "subtrees": done1},
+                "direct_all_cores": {"coeffs_per_s": dv, "threads": threads, "seconds": del_, "masks": ddone},
+                "direct_1_core": {"coeffs_per_s": dv1, "threads": 1, "seconds": del1, "masks": ddone1},
+                "fwht_check_all_cores_extra": {"coeffs_per_s": (1 << (2 * N_QUBITS)) / fw, "threads": threads,
+                                               "seconds": fw, "note": "textbook FWHT check (not the paper's "
+                                                                      "method), whole n=14 matrix"}}}
+
+
+def path_accuracy(A_h, rows, xs):
+    """Max relative error of each path's coefficients against the FP64 oracle on the
+    sampled masks xs: max|c - c_ref| / max|c_ref| over those rows.  Runs after every
+    GPU measurement, in the same host-side leg as the CPU baseline."""
+    import oracle
+    ref = oracle.fwht(A_h, xs=xs)
+    den = float(np.max(np.abs(ref)))
+    out = {}
+    for p, got in rows.items():
+        err = float(np.max(np.abs(got.astype(np.complex128) - ref))) / den
+        out[p] = {"max_rel_err": err, "tolerance": TOLERANCE[p], "within": err <= TOLERANCE[p],
+                  "masks": len(xs), "reference": "oracle FWHT check in FP64 on the same complex64 input"}
+    return out
 
 
 def run_reference(args):
@@ -446,6 +547,10 @@ def main():
         if world > 1:
             dist.barrier()
     total_ms = t0.elapsed_time(t1)
+    # sampled rows of every path's output, checked against the oracle at the end
+    xs = workloads.sample_masks(N_QUBITS, SEED, count=126)
+    xs_t = torch.from_numpy(xs.astype(np.int64)).to(dev)
+    acc_rows = {prec: C[xs_t].cpu().numpy()}
     launch_ms = [a.elapsed_time(b) for a, b in ev]
     kern_ms = float(np.mean(launch_ms))
     ms_per_step, value = job_throughput(total_ms, args.steps, ncoef, world, dev)
@@ -466,7 +571,7 @@ def main():
             "metric": METRIC, "value": value, "unit": "coeffs/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp32": "f32", "fp64": "f64", "bf16x3": "bf16x3->f32", "fp16x2": "fp16x2->f32"}[prec],
+            "dtype": {"fp32": "f32", "fp64": "f64", "bf16x3": "bf16x3->f32", "fixed": "i128"}[prec],
             "data": "synthetic",
             "config": {"workload": f"dense n={N_QUBITS} {1 << N_QUBITS}x{1 << N_QUBITS} complex64 N(0,1), "
                                    f"seed {SEED if N_QUBITS == 14 else N_QUBITS} (+rank)",
@@ -516,7 +621,8 @@ def main():
 
     # the other arithmetic paths on the same input, for context
     if rank == 0 and not args.no_extra_paths:
-        extra = {}
+        extra = {prec: {"coeffs_per_s": ncoef / (kern_ms * 1e-3), "ms": kern_ms, "algorithmic_gbs": achieved,
+                        "note": "the headline path, timed above"}}
         for p2, od in (("fp64", torch.complex128), ("fp32", torch.complex64), ("bf16x3", torch.complex64)):
             if p2 == prec:
                 continue
@@ -537,16 +643,30 @@ def main():
                 ms = a.elapsed_time(b) / reps
                 extra[p2] = {"coeffs_per_s": ncoef / (ms * 1e-3), "ms": ms,
                              "algorithmic_gbs": (in_b + C2.element_size() * C2.numel()) / ms / 1e6}
+                acc_rows[p2] = C2[xs_t].cpu().numpy()
                 del C2, ws2
             except Exception as e:  # report, never hide
                 extra[p2] = {"error": str(e)}
         result["paths"] = extra
-        result["rows"] = measure_rows(dev, stream, hbm_peak, args.rows, args.batched_count)
+        fp64_rate = fp64_add_rate(dev, stream)
+        result["fp64_add_rate"] = {"adds_per_s": fp64_rate, "source": "measured in this run "
+                                   "(ptdr_probe_fp64_adds: 8 add chains per thread, 8 CTAs x 256 threads per SM)"}
+        result["rows"] = measure_rows(dev, stream, hbm_peak, fp64_rate, args.rows, args.batched_count)
     elif rank == 0 and args.rows != "all":
-        result["rows"] = measure_rows(dev, stream, hbm_peak, args.rows, args.batched_count)
+        fp64_rate = fp64_add_rate(dev, stream)
+        result["rows"] = measure_rows(dev, stream, hbm_peak, fp64_rate, args.rows, args.batched_count)
 
-    if rank == 0 and world == 1 and N_QUBITS == 14 and not args.no_cpu_baseline:
-        result["cpu_baseline"] = cpu_baseline()
+    # host-side oracle leg (after every GPU measurement): accuracy of each path on
+    # the sampled masks, then the CPU baseline
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        acc = path_accuracy(A_h, acc_rows, xs)
+        result["accuracy"] = acc
+        result["roofline"]["max_rel_err"] = acc[prec]["max_rel_err"]
+        for p2, e in acc.items():
+            if p2 in result.get("paths", {}):
+                result["paths"][p2].update({"max_rel_err": e["max_rel_err"], "tolerance": e["tolerance"]})
+        if N_QUBITS == 14:
+            result["cpu_baseline"] = cpu_baseline()
 
     if rank == 0:
         print(json.dumps(result))

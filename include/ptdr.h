@@ -76,8 +76,13 @@ typedef enum {
     /* Hadamard stages as dense +-1 tensor-core tiles on bf16 hi/mid/lo splits
        of float32 data, accumulated in float32 (the +-1 matrix is exact in bf16) */
     PTDR_PREC_SPLIT_BF16_TC = 2,
-    /* same with fp16 hi/lo splits of power-of-two-scaled float32 data */
-    PTDR_PREC_SPLIT_FP16_TC = 3
+    /* exact transform in 128-bit two's-complement fixed point on the integer
+       pipe: the input is rounded once to 2^-(124-n) of its largest magnitude
+       (one shared exponent from a pre-pass), every butterfly is an exact
+       integer add, and each result is rounded once to the output type, so the
+       result has FP64 accuracy without the FP64 pipe (dense decompose and
+       compose; inputs must be finite) */
+    PTDR_PREC_FIXED_I128 = 3
 } ptdr_precision;
 
 typedef enum {
@@ -97,7 +102,9 @@ typedef enum {
  *               is rounded to float32 on load).  SPLIT_BF16_TC: n = 14,
  *               a_type = c_type = C64, with A, C and the workspace 32-byte
  *               aligned (PTDR_ERR_INVALID_ARG otherwise); other n or types
- *               return PTDR_ERR_UNSUPPORTED.  SPLIT_FP16_TC: unsupported.
+ *               return PTDR_ERR_UNSUPPORTED.  FIXED_I128: any a_type/c_type
+ *               (a non-finite input entry is recorded as PTDR_ERR_INVALID_ARG
+ *               in the device status word and the output is then undefined).
  *   workspace   device scratch of at least ptdr_workspace_size() bytes (may
  *               be NULL when that size is 0).
  * Returns PTDR_OK once the work is enqueued on `stream`.
@@ -115,7 +122,9 @@ ptdr_status ptdr_decompose(const void* A, ptdr_dtype a_type, void* C, ptdr_dtype
  *
  *   C, c_type   device, 4^n coefficients, c_type in {C64, C128}.
  *   A, a_type   device output, 4^n elements, a_type in {C64, C128}.
- *   n, prec, workspace, stream as for ptdr_decompose (SPLIT_*_TC unsupported).
+ *   n, prec, workspace, stream as for ptdr_decompose (SPLIT_BF16_TC unsupported;
+ *               FIXED_I128 applies a power-of-two scale exactly and any
+ *               other scale with one final FP64 multiply).
  */
 ptdr_status ptdr_compose(const void* C, ptdr_dtype c_type, void* A, ptdr_dtype a_type, int n,
                          double scale, ptdr_precision prec, void* workspace,
@@ -262,6 +271,18 @@ ptdr_status ptdr_decompose_host_scratch_size(int n, ptdr_dtype a_type, ptdr_dtyp
  * the kernels wrote since the previous call (PTDR_OK if none) and clears it.
  */
 ptdr_status ptdr_last_device_status(void* stream);
+
+/*
+ * ptdr_probe_fp64_adds -- measurement helper, not part of the method (the
+ * paper has no counterpart).  Enqueues an FP64 add-chain kernel of `blocks`
+ * CTAs x `threads` threads, each running 8 independent chains of `iters`
+ * dependent adds, and returns in *adds the number of FP64 adds it performs.
+ * Timing it with events on `stream` gives the device's FP64 add rate, the
+ * bound of the FP64 transforms.  d_sink: device scratch of `blocks` doubles
+ * (never written in practice; it keeps the chains live).
+ */
+ptdr_status ptdr_probe_fp64_adds(void* d_sink, int blocks, int threads, int iters, double* adds,
+                                 void* stream);
 
 /* Human-readable name of a status code (static string, never NULL). */
 const char* ptdr_status_string(ptdr_status status);

@@ -33,11 +33,13 @@ def _load():
         lib.oracle_direct.argtypes = [i, vp, vp, u64, vp, i]
         lib.oracle_tree.argtypes = [i, vp, vp, i, u64, u64, i]
         lib.oracle_compose.argtypes = [i, vp, ctypes.c_double, vp, i]
+        lib.oracle_compose_fwht.argtypes = [i, vp, vp, u64, ctypes.c_double, vp, i]
         lib.oracle_fwht.argtypes = [i, vp, vp, u64, vp, i]
         lib.oracle_band_direct.argtypes = [i, i, vp, vp, u64, vp, i]
         lib.oracle_band_fwht.argtypes = [i, i, vp, vp, u64, vp, i]
         lib.oracle_band_masks.argtypes = [i, i, vp, u64, _u64p]
-        for f in ("oracle_brute", "oracle_direct", "oracle_tree", "oracle_compose", "oracle_fwht",
+        for f in ("oracle_brute", "oracle_direct", "oracle_tree", "oracle_compose", "oracle_compose_fwht",
+                  "oracle_fwht",
                   "oracle_band_direct", "oracle_band_fwht", "oracle_band_masks", "oracle_max_threads"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
@@ -112,6 +114,28 @@ def compose(C, scale=1.0, threads=0):
     A = np.zeros((N, N), np.complex128)
     _check(_load().oracle_compose(n, _ptr(C), float(scale), _ptr(A), threads), "compose")
     return A
+
+
+def compose_fwht(C, scale=1.0, xs=None, threads=0):
+    """Inverse map A = scale * sum_P c_P P for large n: per mask, phase i^{|x&z|},
+    textbook FWHT over z, XOR-scatter (pinned against ``compose``).
+
+    ``xs=None``: C is the whole coefficient array; returns A.  Otherwise C holds
+    one row of coefficients per mask in ``xs`` and row i of the result is the
+    XOR-diagonal ``A[k ^ xs[i], k]`` over k (a few masks of a large matrix)."""
+    C = np.ascontiguousarray(C, dtype=np.complex128)
+    N = C.shape[1]
+    if C.ndim != 2 or N < 2 or N & (N - 1) or (xs is None and C.shape[0] != N):
+        raise ValueError("C must hold rows of 2^n coefficients")
+    n = N.bit_length() - 1
+    if xs is not None:
+        xs = np.ascontiguousarray(xs, dtype=np.uint64)
+        if len(xs) != C.shape[0]:
+            raise ValueError("one coefficient row per mask")
+    out = np.zeros((N if xs is None else len(xs), N), np.complex128)
+    _check(_load().oracle_compose_fwht(n, _ptr(C), _ptr(xs), 0 if xs is None else len(xs), float(scale),
+                                       _ptr(out), threads), "compose_fwht")
+    return out
 
 
 def fwht(A, xs=None, threads=0):

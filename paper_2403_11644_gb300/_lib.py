@@ -15,7 +15,7 @@ STATUS_NAMES = {
     4: "PTDR_ERR_CUDA", 5: "PTDR_ERR_WORKSPACE", 6: "PTDR_ERR_TIMEOUT", 7: "PTDR_ERR_INTERNAL",
 }
 C64, C128, F32, F64 = 0, 1, 2, 3
-PREC_FP64, PREC_FP32, PREC_SPLIT_BF16_TC, PREC_SPLIT_FP16_TC = 0, 1, 2, 3
+PREC_FP64, PREC_FP32, PREC_SPLIT_BF16_TC, PREC_FIXED_I128 = 0, 1, 2, 3
 OP_DECOMPOSE, OP_COMPOSE = 0, 1
 
 _lock = threading.Lock()
@@ -45,6 +45,7 @@ SIGNATURES = {
     "ptdr_decompose_host": [_vp, _vp, _i, _i, _i, _i, _i, _vp, _sz, _vp],
     "ptdr_decompose_host_scratch_size": [_i, _i, _i, _i, _szp],
     "ptdr_last_device_status": [_vp],
+    "ptdr_probe_fp64_adds": [_vp, _i, _i, _i, ctypes.POINTER(ctypes.c_double), _vp],
     "ptdr_status_string": [_i],
     "ptdr_version": [],
 }

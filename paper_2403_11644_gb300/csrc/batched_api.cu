@@ -18,7 +18,7 @@ ptdr_status validate_batched(const int* h_n, int count, ptdr_dtype a_t, ptdr_dty
     if (!h_n || count < 1 || count > (1 << 20)) return PTDR_ERR_INVALID_ARG;
     if ((int)a_t < PTDR_C64 || (int)a_t > PTDR_F64 || (int)c_t < PTDR_C64 || (int)c_t > PTDR_F64)
         return PTDR_ERR_INVALID_ARG;
-    if ((int)prec < PTDR_PREC_FP64 || (int)prec > PTDR_PREC_SPLIT_FP16_TC) return PTDR_ERR_INVALID_ARG;
+    if ((int)prec < PTDR_PREC_FP64 || (int)prec > PTDR_PREC_FIXED_I128) return PTDR_ERR_INVALID_ARG;
     if (!dtype_complex(a_t) || !dtype_complex(c_t)) return PTDR_ERR_UNSUPPORTED;
     if (prec != PTDR_PREC_FP64 && prec != PTDR_PREC_FP32) return PTDR_ERR_UNSUPPORTED;
     long long total = 0;

@@ -1,0 +1,501 @@
+// Exact fixed-point path (PTDR_PREC_FIXED_I128): the FP64-accuracy mode that
+// does not use the FP64 pipe.
+//
+// The Walsh-Hadamard transform of Sec. II.A's sparse trace (per mask x,
+// c_{x,z} = 2^-n (-i)^{|x&z|} sum_k (-1)^{|z&k|} A[k^x][k]) and of the inverse
+// map is a sum of +-1 multiples of the inputs, so in two's-complement fixed
+// point it is exact.  With E the binary exponent bound of the input
+// (every |Re|, |Im| < 2^E, from a max pre-pass over the whole input) each
+// real input v becomes the 128-bit integer X = round(v 2^S), S = 124 - n - E:
+// |X| < 2^(124-n), and a sum of 2^n such values stays below 2^124, inside
+// 127 bits.  The transform is then integer adds (no rounding at all), and
+// each result is rounded once to the output type.  The only error is the
+// input rounding below 2^-(124-n) of the largest input and the final
+// rounding.
+//
+// GB300's FP64 pipe is slow (about 0.5 T adds/s, the bound of the FP64
+// path); nothing here uses it: inputs are decoded from their IEEE bit fields
+// and outputs encoded the same way, with integer shifts and round-to-nearest-
+// even done on the integers.  Only a compose scale that is not a power of two
+// costs one FP64 multiply per output value.
+//
+// Kernels: a pre-pass (maximum exponent field of the input), the tile kernel
+// (gather or phased row load, radix-8 transform passes in shared memory,
+// phased write-out / intermediate rows / XOR-scatter) and the strided pass
+// over the high bits, which reads and writes 32-byte fixed-point complex
+// values of an intermediate in the workspace (chunks of masks small enough to
+// stay in L2).
+#include <algorithm>
+#include <cmath>
+
+#include "fixed_point.cuh"
+#include "plan.h"
+#include "tile_ops.cuh"
+
+namespace ptdr {
+
+using fxp::i128;
+using fxp::fixed_of;
+using fxp::f32_bits;
+using fxp::f64_bits;
+
+// A complex value in 128-bit fixed point (real, imaginary).
+struct __align__(16) fx2 {
+    i128 x, y;
+};
+
+__device__ __forceinline__ fx2 cadd(fx2 a, fx2 b)
+{
+    a.x += b.x;
+    a.y += b.y;
+    return a;
+}
+__device__ __forceinline__ fx2 csub(fx2 a, fx2 b)
+{
+    a.x -= b.x;
+    a.y -= b.y;
+    return a;
+}
+
+namespace {
+
+template <typename InT> struct in_of;
+template <> struct in_of<float2> {
+    static constexpr int bias = 127;
+    __device__ static __forceinline__ fx2 cvt(float2 v, int S) { return fx2{fixed_of(v.x, S), fixed_of(v.y, S)}; }
+};
+template <> struct in_of<double2> {
+    static constexpr int bias = 1023;
+    __device__ static __forceinline__ fx2 cvt(double2 v, int S) { return fx2{fixed_of(v.x, S), fixed_of(v.y, S)}; }
+};
+
+// How the fixed-point results become output values: value = X 2^(q_pow - S),
+// times `mul` when the scale is not a power of two.
+struct FxOut {
+    int q;
+    double mul;
+    bool use_mul;
+};
+
+// Output value (-i)^p * X 2^q (* mul): an odd p swaps the parts, the real part
+// changes sign for p = 2, 3 and the imaginary part for p = 1, 2 (sign bits).
+template <typename OutT> struct out_of;
+template <> struct out_of<double2> {
+    __device__ static __forceinline__ double2 cvt(fx2 v, int p, const FxOut& o)
+    {
+        const bool odd = (p & 1) != 0;
+        uint64_t re = f64_bits(odd ? v.y : v.x, o.q), im = f64_bits(odd ? v.x : v.y, o.q);
+        re ^= (uint64_t)((p >> 1) & 1) << 63;
+        im ^= (uint64_t)((p ^ (p >> 1)) & 1) << 63;
+        double2 r = make_double2(__longlong_as_double((long long)re), __longlong_as_double((long long)im));
+        if (o.use_mul) {
+            r.x *= o.mul;
+            r.y *= o.mul;
+        }
+        return r;
+    }
+};
+template <> struct out_of<float2> {
+    __device__ static __forceinline__ float2 cvt(fx2 v, int p, const FxOut& o)
+    {
+        const bool odd = (p & 1) != 0;
+        if (o.use_mul) { // round once to double, scale, round to float
+            const double2 d = out_of<double2>::cvt(v, p, o);
+            return make_float2((float)d.x, (float)d.y);
+        }
+        uint32_t re = f32_bits(odd ? v.y : v.x, o.q), im = f32_bits(odd ? v.x : v.y, o.q);
+        re ^= (uint32_t)((p >> 1) & 1) << 31;
+        im ^= (uint32_t)((p ^ (p >> 1)) & 1) << 31;
+        return make_float2(__uint_as_float(re), __uint_as_float(im));
+    }
+};
+
+// i^p times a fixed-point value (exact: swaps and negations).
+__device__ __forceinline__ fx2 times_i_pow(fx2 v, int p)
+{
+    // i^p = (-i)^m with m = 4 - p (mod 4); (-i)^m: an odd m swaps the parts,
+    // the real part changes sign for m = 2, 3 and the imaginary part for m = 1, 2
+    const int m = (4 - (p & 3)) & 3;
+    const bool odd = (m & 1) != 0;
+    const i128 u = odd ? v.y : v.x, w = odd ? v.x : v.y;
+    return fx2{(m & 2) ? -u : u, ((m ^ (m >> 1)) & 1) ? -w : w};
+}
+
+} // namespace
+
+struct FxLaunch {
+    const void* src;
+    void* dst;
+    Load load;
+    Store store;
+    int n;
+    int log_r, log_l;    // tile kernel: masks x segment
+    int b0, b1, log_w;   // strided kernel: bits [b0, b1), 2^log_w columns
+    uint64_t x_begin, x_count, dst_row0, src_row0, src_elems, dst_elems;
+    const int* emax;     // largest exponent field of the original input (pre-pass)
+    int bias;            // exponent bias of the original input's type
+    int q_pow;           // output value = X 2^(q_pow - S) (* mul)
+    double mul;
+    bool use_mul;
+};
+
+namespace {
+
+// Exponent bound E of the original input (every |value| < 2^E) and the shift S.
+__device__ __forceinline__ int fx_shift(const FxLaunch& p)
+{
+    const int f = *p.emax;
+    const int E = f ? f - p.bias + 1 : 1 - p.bias;
+    return 124 - p.n - E;
+}
+
+__device__ __forceinline__ FxOut fx_out(const FxLaunch& p, int S) { return FxOut{p.q_pow - S, p.mul, p.use_mul}; }
+
+// ----------------------------------------------------------------- pre-pass
+
+// Largest exponent field over `words` machine words of real values (32-bit
+// words for float data, 64-bit for double); a non-finite value is an argument
+// error recorded in the status word.
+template <typename W>
+__global__ void __launch_bounds__(256) k_fx_maxexp(const W* __restrict__ v, uint64_t words, int* emax, unsigned int* st)
+{
+    constexpr int kShift = sizeof(W) == 4 ? 23 : 52;
+    constexpr uint32_t kMask = sizeof(W) == 4 ? 0xFFu : 0x7FFu;
+    uint32_t best = 0;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    constexpr int kU = 8;
+    uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + (kU - 1) * stride < words; i += kU * stride) {
+        W w[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) w[u] = __ldcs(v + i + u * stride);
+#pragma unroll
+        for (int u = 0; u < kU; ++u) best = max(best, (uint32_t)(w[u] >> kShift) & kMask);
+    }
+    for (; i < words; i += stride) best = max(best, (uint32_t)(__ldcs(v + i) >> kShift) & kMask);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if ((threadIdx.x & 31) == 0 && best) {
+        if (best == kMask) report_status(st, PTDR_ERR_INVALID_ARG);
+        atomicMax(emax, (int)best);
+    }
+}
+
+// ------------------------------------------------------------- tile kernel
+
+template <typename InT, Load LD>
+__device__ void fx_load(fx2* s, const Smem& sm, const FxLaunch& p, uint64_t x0, uint64_t k0, int S, unsigned int* st)
+{
+    const uint64_t N = 1ull << p.n;
+    const int log_r = p.log_r, log_l = p.log_l;
+    const uint64_t R = 1ull << log_r, L = 1ull << log_l;
+    const int E = 1 << (log_r + log_l);
+    for (int e0 = threadIdx.x; e0 < E; e0 += kLoadBatch * blockDim.x) {
+        InT v[kLoadBatch];
+        fx2 f[kLoadBatch];
+        int dst[kLoadBatch];
+        int ph[kLoadBatch];
+#pragma unroll
+        for (int u = 0; u < kLoadBatch; ++u) {
+            const int e = e0 + u * blockDim.x;
+            dst[u] = -1;
+            ph[u] = 0;
+            if (e >= E) continue;
+            if constexpr (LD == Load::GatherA) {
+                // row r of A supplies the aligned block of 2^log_r columns r ^ x
+                const uint64_t rb = (k0 ^ x0) & ~(L - 1);
+                const uint64_t r = rb + ((uint64_t)e >> log_r);
+                const uint64_t c = ((r ^ x0) & ~(R - 1)) + ((uint64_t)e & (R - 1));
+                const uint64_t gi = r * N + c;
+                dst[u] = sm.idx((int)(((r ^ c) - x0) << log_l) + (int)(c - k0));
+                if (in_bounds(st, gi, p.src_elems)) v[u] = __ldg((const InT*)p.src + gi);
+                else dst[u] = -2;
+            } else {
+                const uint64_t x = x0 + (uint64_t)(e >> log_l);
+                const uint64_t z = k0 + (uint64_t)(e & ((1 << log_l) - 1));
+                const uint64_t gi = (x - p.src_row0) * N + z;
+                dst[u] = sm.idx(e);
+                ph[u] = __popcll(x & z);
+                if (!in_bounds(st, gi, p.src_elems)) dst[u] = -2;
+                else if constexpr (LD == Load::RowBuf) f[u] = ((const fx2*)p.src)[gi];
+                else v[u] = __ldg((const InT*)p.src + gi);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kLoadBatch; ++u) {
+            if (dst[u] == -1) continue;
+            const int d = dst[u] == -2 ? -1 : dst[u];
+            fx2 w;
+            if constexpr (LD == Load::RowBuf)
+                w = f[u];
+            else if constexpr (LD == Load::RowPhaseC)
+                w = times_i_pow(in_of<InT>::cvt(v[u], S), ph[u]);
+            else
+                w = in_of<InT>::cvt(v[u], S);
+            if (d >= 0) s[d] = w;
+        }
+    }
+}
+
+template <typename OutT, Store ST>
+__device__ void fx_store(const fx2* s, const Smem& sm, const FxLaunch& p, uint64_t x0, uint64_t k0, int S,
+                         unsigned int* st)
+{
+    const uint64_t N = 1ull << p.n;
+    const int log_r = p.log_r, log_l = p.log_l;
+    const uint64_t R = 1ull << log_r, L = 1ull << log_l;
+    const int E = 1 << (log_r + log_l);
+    const FxOut o = fx_out(p, S);
+    for (int e = threadIdx.x; e < E; e += blockDim.x) {
+        if constexpr (ST == Store::ScatterA) {
+            const uint64_t rb = (k0 ^ x0) & ~(L - 1);
+            const uint64_t r = rb + ((uint64_t)e >> log_r);
+            const uint64_t c = ((r ^ x0) & ~(R - 1)) + ((uint64_t)e & (R - 1));
+            const uint64_t gi = r * N + c;
+            const fx2 v = s[sm.idx((int)(((r ^ c) - x0) << log_l) + (int)(c - k0))];
+            if (in_bounds(st, gi, p.dst_elems)) ((OutT*)p.dst)[gi] = out_of<OutT>::cvt(v, 0, o);
+        } else {
+            const uint64_t x = x0 + (uint64_t)(e >> log_l);
+            const uint64_t z = k0 + (uint64_t)(e & ((1 << log_l) - 1));
+            const uint64_t gi = (x - p.dst_row0) * N + z;
+            const fx2 v = s[sm.idx(e)];
+            if (!in_bounds(st, gi, p.dst_elems)) continue;
+            if constexpr (ST == Store::RowBuf)
+                ((fx2*)p.dst)[gi] = v;
+            else
+                ((OutT*)p.dst)[gi] = out_of<OutT>::cvt(v, __popcll(x & z) & 3, o);
+        }
+    }
+}
+
+template <typename InT, typename OutT, Load LD, Store ST>
+__global__ void __launch_bounds__(512) k_fx_tile(FxLaunch p, unsigned int* st)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    fx2* s = reinterpret_cast<fx2*>(smem_raw);
+    const Smem sm = make_smem(p.log_l);
+    const int segs_log = p.n - p.log_l;
+    const uint64_t blk = (uint64_t)blockIdx.x >> segs_log;
+    const uint64_t seg = (uint64_t)blockIdx.x & ((1ull << segs_log) - 1);
+    const uint64_t x0 = p.x_begin + (blk << p.log_r);
+    const uint64_t k0 = seg << p.log_l;
+    const int S = fx_shift(p);
+    fx_load<InT, LD>(s, sm, p, x0, k0, S, st);
+    __syncthreads();
+    wht_bits<3>(s, sm, p.log_r + p.log_l, 0, p.log_l);
+    fx_store<OutT, ST>(s, sm, p, x0, k0, S, st);
+}
+
+// One CTA per (mask, group of bits >= b1, chunk of 2^log_w low columns) of an
+// intermediate of fixed-point rows; transform over bits [b0, b1).
+template <typename OutT, Store ST>
+__global__ void __launch_bounds__(512) k_fx_strided(FxLaunch p, unsigned int* st)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    fx2* s = reinterpret_cast<fx2*>(smem_raw);
+    const int nb = p.b1 - p.b0;
+    const Smem sm = make_smem(p.log_w);
+    const uint64_t N = 1ull << p.n;
+    const int chunks_log = p.b0 - p.log_w;
+    const int groups_log = p.n - p.b1;
+    uint64_t id = blockIdx.x;
+    const uint64_t chunk = id & ((1ull << chunks_log) - 1);
+    id >>= chunks_log;
+    const uint64_t g = id & ((1ull << groups_log) - 1);
+    id >>= groups_log;
+    const uint64_t x = p.x_begin + id;
+    const uint64_t kbase = (g << p.b1) + (chunk << p.log_w);
+    const fx2* src = (const fx2*)p.src + (x - p.src_row0) * N;
+    const int E = 1 << (nb + p.log_w);
+    const int wmask = (1 << p.log_w) - 1;
+    for (int e0 = threadIdx.x; e0 < E; e0 += kLoadBatch * blockDim.x) {
+        fx2 v[kLoadBatch];
+#pragma unroll
+        for (int u = 0; u < kLoadBatch; ++u) {
+            const int e = e0 + u * blockDim.x;
+            v[u] = fx2{0, 0};
+            if (e < E) {
+                const uint64_t k = kbase + ((uint64_t)(e >> p.log_w) << p.b0) + (uint64_t)(e & wmask);
+                if (in_bounds(st, (x - p.src_row0) * N + k, p.src_elems)) v[u] = src[k];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kLoadBatch; ++u) {
+            const int e = e0 + u * blockDim.x;
+            if (e < E) s[sm.idx(e)] = v[u];
+        }
+    }
+    __syncthreads();
+    wht_bits<3>(s, sm, nb + p.log_w, p.log_w, nb + p.log_w);
+    const int S = fx_shift(p);
+    const FxOut o = fx_out(p, S);
+    for (int e = threadIdx.x; e < E; e += blockDim.x) {
+        const uint64_t k = kbase + ((uint64_t)(e >> p.log_w) << p.b0) + (uint64_t)(e & wmask);
+        const fx2 v = s[sm.idx(e)];
+        if constexpr (ST == Store::RowPhaseOut) {
+            const uint64_t gi = (x - p.dst_row0) * N + k;
+            if (in_bounds(st, gi, p.dst_elems))
+                ((OutT*)p.dst)[gi] = out_of<OutT>::cvt(v, __popcll(x & k) & 3, o);
+        } else if constexpr (ST == Store::RowBuf) {
+            const uint64_t gi = (x - p.dst_row0) * N + k;
+            if (in_bounds(st, gi, p.dst_elems)) ((fx2*)p.dst)[gi] = v;
+        } else {
+            const uint64_t gi = (k ^ x) * N + k;
+            if (in_bounds(st, gi, p.dst_elems)) ((OutT*)p.dst)[gi] = out_of<OutT>::cvt(v, 0, o);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ launch
+
+template <typename K>
+cudaError_t fx_smem(K kernel, size_t bytes)
+{
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <typename InT, typename OutT, Load LD, Store ST>
+cudaError_t run_fx_tile(const FxLaunch& p, unsigned int* st, cudaStream_t s)
+{
+    auto kern = k_fx_tile<InT, OutT, LD, ST>;
+    const size_t bytes = smem_elems((size_t)1 << p.log_r, p.log_l) * sizeof(fx2);
+    cudaError_t e = fx_smem(kern, bytes);
+    if (e != cudaSuccess) return e;
+    const uint64_t blocks = (p.x_count >> p.log_r) << (p.n - p.log_l);
+    kern<<<(unsigned)blocks, 512, bytes, s>>>(p, st);
+    return cudaGetLastError();
+}
+
+template <typename OutT, Store ST>
+cudaError_t run_fx_strided(const FxLaunch& p, unsigned int* st, cudaStream_t s)
+{
+    auto kern = k_fx_strided<OutT, ST>;
+    const size_t bytes = smem_elems((size_t)1 << (p.b1 - p.b0), p.log_w) * sizeof(fx2);
+    cudaError_t e = fx_smem(kern, bytes);
+    if (e != cudaSuccess) return e;
+    const uint64_t blocks = p.x_count << ((p.n - p.b1) + (p.b0 - p.log_w));
+    kern<<<(unsigned)blocks, 512, bytes, s>>>(p, st);
+    return cudaGetLastError();
+}
+
+// Dispatch on (input type, output type) for a given load/store pair.
+template <Load LD, Store ST>
+cudaError_t fx_tile_types(const FxLaunch& p, ptdr_dtype in_t, ptdr_dtype out_t, unsigned int* st, cudaStream_t s)
+{
+    const bool i64 = in_t == PTDR_C128, o64 = out_t == PTDR_C128;
+    if (i64) return o64 ? run_fx_tile<double2, double2, LD, ST>(p, st, s) : run_fx_tile<double2, float2, LD, ST>(p, st, s);
+    return o64 ? run_fx_tile<float2, double2, LD, ST>(p, st, s) : run_fx_tile<float2, float2, LD, ST>(p, st, s);
+}
+
+template <Store ST>
+cudaError_t fx_strided_types(const FxLaunch& p, ptdr_dtype out_t, unsigned int* st, cudaStream_t s)
+{
+    return out_t == PTDR_C128 ? run_fx_strided<double2, ST>(p, st, s) : run_fx_strided<float2, ST>(p, st, s);
+}
+
+} // namespace
+
+size_t fixed_ws_header() { return 256; }
+
+// The whole fixed-point decompose / compose of one matrix: the exponent
+// pre-pass over the input, then single tile passes (rows that fit) or, per
+// chunk of masks, a first pass into the intermediate and strided passes.
+cudaError_t launch_fixed(const DensePlan& plan, const void* in, void* out, void* ws, double scale, unsigned int* st,
+                         cudaStream_t s)
+{
+    const uint64_t N = 1ull << plan.n;
+    int* emax = (int*)ws;
+    cudaError_t e = cudaMemsetAsync(ws, 0, fixed_ws_header(), s);
+    if (e != cudaSuccess) return e;
+    const bool in64 = plan.in_t == PTDR_C128;
+    {
+        int dev = 0, sms = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        const uint64_t words = 2 * N * N;
+        const unsigned grid = (unsigned)std::min<uint64_t>((uint64_t)sms * 8, std::max<uint64_t>(1, words / 256));
+        if (in64)
+            k_fx_maxexp<uint64_t><<<grid, 256, 0, s>>>((const uint64_t*)in, words, emax, st);
+        else
+            k_fx_maxexp<uint32_t><<<grid, 256, 0, s>>>((const uint32_t*)in, words, emax, st);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    FxLaunch p{};
+    p.n = plan.n;
+    p.emax = emax;
+    p.bias = in64 ? 1023 : 127;
+    // output value = X 2^-S times 2^-n (decompose) or times the compose scale
+    if (!plan.compose) {
+        p.q_pow = -plan.n;
+    } else {
+        int ex = 0;
+        const double m = std::frexp(scale, &ex);
+        if (m == 0.5 || m == -0.5) {
+            p.q_pow = ex - 1;
+            p.use_mul = m < 0;
+            p.mul = -1.0;
+        } else {
+            p.q_pow = 0;
+            p.use_mul = true;
+            p.mul = scale;
+        }
+    }
+    const Load ld = plan.compose ? Load::RowPhaseC : Load::GatherA;
+    if (plan.single) {
+        p.src = in;
+        p.dst = out;
+        p.log_r = plan.log_r;
+        p.log_l = plan.log_l;
+        p.x_begin = 0;
+        p.x_count = N;
+        p.src_elems = p.dst_elems = N * N;
+        if (plan.compose) return fx_tile_types<Load::RowPhaseC, Store::ScatterA>(p, plan.in_t, plan.out_t, st, s);
+        return fx_tile_types<Load::GatherA, Store::RowPhaseOut>(p, plan.in_t, plan.out_t, st, s);
+    }
+    fx2* buf = (fx2*)((char*)ws + fixed_ws_header());
+    for (uint64_t x0 = 0; x0 < N && e == cudaSuccess; x0 += plan.chunk) {
+        FxLaunch t = p;
+        t.src = in;
+        t.dst = buf;
+        t.load = ld;
+        t.store = Store::RowBuf;
+        t.log_r = plan.log_r;
+        t.log_l = plan.log_l;
+        t.x_begin = x0;
+        t.x_count = plan.chunk;
+        t.dst_row0 = x0;
+        t.src_row0 = 0;
+        t.src_elems = N * N;
+        t.dst_elems = plan.chunk * N;
+        e = plan.compose ? fx_tile_types<Load::RowPhaseC, Store::RowBuf>(t, plan.in_t, plan.out_t, st, s)
+                         : fx_tile_types<Load::GatherA, Store::RowBuf>(t, plan.in_t, plan.out_t, st, s);
+        for (size_t i = 0; i < plan.passes.size() && e == cudaSuccess; ++i) {
+            const bool last = i + 1 == plan.passes.size();
+            FxLaunch q = p;
+            q.src = buf;
+            q.b0 = plan.passes[i].b0;
+            q.b1 = plan.passes[i].b1;
+            q.log_w = plan.passes[i].log_w;
+            q.x_begin = x0;
+            q.x_count = plan.chunk;
+            q.src_row0 = x0;
+            q.src_elems = plan.chunk * N;
+            if (!last) {
+                q.dst = buf;
+                q.dst_row0 = x0;
+                q.dst_elems = plan.chunk * N;
+                e = fx_strided_types<Store::RowBuf>(q, plan.out_t, st, s);
+            } else {
+                q.dst = out;
+                q.dst_row0 = 0;
+                q.dst_elems = N * N;
+                e = plan.compose ? fx_strided_types<Store::ScatterA>(q, plan.out_t, st, s)
+                                 : fx_strided_types<Store::RowPhaseOut>(q, plan.out_t, st, s);
+            }
+        }
+    }
+    return e;
+}
+
+} // namespace ptdr

@@ -33,7 +33,37 @@ std::vector<StridedPass> strided_schedule(int b0, int n, size_t elem_bytes)
 ptdr_status make_dense_plan(bool compose, int n, ptdr_dtype in_t, ptdr_dtype out_t,
                             ptdr_precision prec, DensePlan* plan)
 {
-    if (prec == PTDR_PREC_SPLIT_FP16_TC) return PTDR_ERR_UNSUPPORTED;
+    if (prec == PTDR_PREC_FIXED_I128) {
+        // 32-byte fixed-point complex values: rows of up to 4096 in one tile,
+        // longer rows as a first pass and strided passes through an
+        // intermediate chunk of masks that stays in L2
+        DensePlan p;
+        p.compose = compose;
+        p.n = n;
+        p.in_t = in_t;
+        p.out_t = out_t;
+        p.prec = prec;
+        p.kernel = DenseKernel::Fixed;
+        const size_t S = 32, N = (size_t)1 << n, row_bytes = N * S;
+        p.threads = 512;
+        if (row_bytes <= kRowTileBytes) {
+            p.single = true;
+            p.log_l = n;
+            int lr = 0;
+            while (lr < 4 && lr < n && (row_bytes << (lr + 1)) <= std::max(row_bytes, kTileBytes)) ++lr;
+            p.log_r = lr;
+            p.ws_bytes = fixed_ws_header();
+        } else {
+            p.single = false;
+            p.log_r = compose ? 0 : 2;
+            p.log_l = ilog2(kTileBytes / S) - p.log_r;
+            p.passes = strided_schedule(p.log_l, n, S);
+            p.chunk = std::max<size_t>((size_t)1 << p.log_r, std::min<size_t>(N, kFixedChunkBytes / row_bytes));
+            p.ws_bytes = fixed_ws_header() + p.chunk * row_bytes;
+        }
+        *plan = p;
+        return PTDR_OK;
+    }
     if (prec == PTDR_PREC_SPLIT_BF16_TC) {
         // the tensor-core path covers the n = 14 complex64 workload
         if (compose || n != 14 || in_t != PTDR_C64 || out_t != PTDR_C64) return PTDR_ERR_UNSUPPORTED;
@@ -123,6 +153,10 @@ ptdr_status execute_dense(const DensePlan& p, const void* in, void* out, void* w
 {
     const uint64_t N = 1ull << p.n;
     cudaError_t e = cudaSuccess;
+    if (p.kernel == DenseKernel::Fixed) {
+        e = launch_fixed(p, in, out, ws, scale, st, s);
+        return e == cudaSuccess ? PTDR_OK : PTDR_ERR_CUDA;
+    }
     if (p.kernel == DenseKernel::Tc14) {
         // 32-byte vector loads and stores of A, C and the staging rows
         if ((uintptr_t)in % 32 || (uintptr_t)out % 32 || (uintptr_t)ws % 32) return PTDR_ERR_INVALID_ARG;

@@ -15,6 +15,8 @@ constexpr size_t kTileBytes = 64 * 1024;
 constexpr size_t kRowTileBytes = 128 * 1024;
 // Workspace cap for the intermediate of chunked multi-pass launches.
 constexpr size_t kChunkBytes = 256ull << 20;
+// Intermediate of the fixed-point path per chunk of masks: small enough to stay in L2.
+constexpr size_t kFixedChunkBytes = 64ull << 20;
 
 struct StridedPass {
     int b0, b1, log_w;
@@ -28,6 +30,7 @@ enum class DenseKernel {
     Compose14,  // n = 14 FP32 compose complex64 -> complex64: staged two-pass kernel
     Rr,         // n = 9 .. 12 FP32 decompose complex64 -> complex64 (16-byte aligned):
                 // register-round items, one CTA per 2^(13-n) masks; otherwise the generic tiles
+    Fixed,      // exact 128-bit fixed-point transform (any n, decompose and compose)
 };
 
 struct DensePlan {
@@ -63,6 +66,9 @@ size_t tc14_pipe_workspace();
 cudaError_t launch_compose14_staged(const void* C, void* A, double scale, void* ws, unsigned int* status,
                                     cudaStream_t s);
 size_t compose14_staged_workspace();
+size_t fixed_ws_header();
+cudaError_t launch_fixed(const DensePlan& plan, const void* in, void* out, void* ws, double scale,
+                         unsigned int* status, cudaStream_t s);
 cudaError_t launch_rr_dense(int n, const void* A, void* C, double scale, unsigned int* status, cudaStream_t s);
 
 // shared helpers (ptdr_api.cu)

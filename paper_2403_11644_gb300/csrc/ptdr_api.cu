@@ -82,7 +82,7 @@ using namespace ptdr;
 namespace {
 
 bool valid_dtype(int t) { return t >= PTDR_C64 && t <= PTDR_F64; }
-bool valid_prec(int p) { return p >= PTDR_PREC_FP64 && p <= PTDR_PREC_SPLIT_FP16_TC; }
+bool valid_prec(int p) { return p >= PTDR_PREC_FP64 && p <= PTDR_PREC_FIXED_I128; }
 
 ptdr_status validate_dense(const void* in, ptdr_dtype in_t, const void* out, ptdr_dtype out_t,
                            int n, ptdr_precision prec, bool compose)
@@ -91,7 +91,7 @@ ptdr_status validate_dense(const void* in, ptdr_dtype in_t, const void* out, ptd
     if (n < 1 || n > kMaxDenseN) return PTDR_ERR_INVALID_ARG;
     if (!valid_dtype(in_t) || !valid_dtype(out_t) || !valid_prec(prec)) return PTDR_ERR_INVALID_ARG;
     if (!dtype_complex(in_t) || !dtype_complex(out_t)) return PTDR_ERR_UNSUPPORTED;
-    if (prec == PTDR_PREC_SPLIT_BF16_TC || prec == PTDR_PREC_SPLIT_FP16_TC) {
+    if (prec == PTDR_PREC_SPLIT_BF16_TC) {
         if (compose) return PTDR_ERR_UNSUPPORTED;
         if (in_t != PTDR_C64 || out_t != PTDR_C64) return PTDR_ERR_UNSUPPORTED;
     }

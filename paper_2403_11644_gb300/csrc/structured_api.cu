@@ -100,7 +100,7 @@ ptdr_status validate_structured(const void* bands, ptdr_dtype b_t, int n, int s,
     if (s >= kMaxBandPairs) return PTDR_ERR_UNSUPPORTED;
     if ((int)b_t < PTDR_C64 || (int)b_t > PTDR_F64 || (int)c_t < PTDR_C64 || (int)c_t > PTDR_F64)
         return PTDR_ERR_INVALID_ARG;
-    if ((int)prec < PTDR_PREC_FP64 || (int)prec > PTDR_PREC_SPLIT_FP16_TC) return PTDR_ERR_INVALID_ARG;
+    if ((int)prec < PTDR_PREC_FP64 || (int)prec > PTDR_PREC_FIXED_I128) return PTDR_ERR_INVALID_ARG;
     if (prec != PTDR_PREC_FP64 && prec != PTDR_PREC_FP32) return PTDR_ERR_UNSUPPORTED;
     if (!dtype_complex(c_t) && dtype_complex(b_t)) return PTDR_ERR_UNSUPPORTED;
     for (size_t i = 0; i < n_masks; ++i)

@@ -69,13 +69,22 @@ __device__ __forceinline__ void wht_pass(T2* s, const Smem& sm, int log_e, int b
     }
 }
 
-// Transform flat-index bits [b0, b1), four at a time, barrier after each.
-template <typename T2>
+// Transform flat-index bits [b0, b1), up to MaxNB (4 or 3) at a time, barrier
+// after each pass (wide value types take 3 bits per pass: 8 values in registers).
+template <int MaxNB = 4, typename T2>
 __device__ void wht_bits(T2* s, const Smem& sm, int log_e, int b0, int b1)
 {
-    for (int b = b0; b < b1; b += 4) {
-        switch (min(4, b1 - b)) {
-        case 4: wht_pass<4>(s, sm, log_e, b); break;
+    static_assert(MaxNB == 3 || MaxNB == 4, "radix-8 or radix-16 passes");
+    for (int b = b0; b < b1; b += MaxNB) {
+        const int nb = min(MaxNB, b1 - b);
+        if constexpr (MaxNB == 4) { // not instantiated for radix-8 types
+            if (nb == 4) {
+                wht_pass<4>(s, sm, log_e, b);
+                __syncthreads();
+                continue;
+            }
+        }
+        switch (nb) {
         case 3: wht_pass<3>(s, sm, log_e, b); break;
         case 2: wht_pass<2>(s, sm, log_e, b); break;
         default: wht_pass<1>(s, sm, log_e, b); break;

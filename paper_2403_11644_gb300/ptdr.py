@@ -20,7 +20,7 @@ PRECISIONS = {
     "fp64": _lib.PREC_FP64,
     "fp32": _lib.PREC_FP32,
     "bf16x3": _lib.PREC_SPLIT_BF16_TC,
-    "fp16x2": _lib.PREC_SPLIT_FP16_TC,
+    "fixed": _lib.PREC_FIXED_I128,
 }
 _DT = {torch.complex64: _lib.C64, torch.complex128: _lib.C128, torch.float32: _lib.F32,
        torch.float64: _lib.F64}
@@ -74,7 +74,7 @@ def decompose(A: torch.Tensor, precision: str = "fp32", out_dtype=None, out=None
     if A.shape != (1 << n, 1 << n):
         raise ValueError("A must be square")
     if out_dtype is None:
-        out_dtype = torch.complex128 if precision == "fp64" else torch.complex64
+        out_dtype = torch.complex128 if precision in ("fp64", "fixed") else torch.complex64
     C = out if out is not None else torch.empty((1 << n, 1 << n), dtype=out_dtype, device=A.device)
     ws_bytes = workspace_size("decompose", n, A.dtype, C.dtype, precision)
     ws = workspace if workspace is not None else (_workspace(ws_bytes, A.device) if ws_bytes else None)

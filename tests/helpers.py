@@ -5,7 +5,7 @@ import torch
 
 # Error bounds: relative max-abs error max|c - c_ref| / max|c_ref| against the
 # FP64 oracle, per arithmetic path.
-TOL = {"fp64": 1e-12, "fp32": 1e-5, "bf16x3": 2e-6, "fp16x2": 2e-6}
+TOL = {"fp64": 1e-12, "fp32": 1e-5, "bf16x3": 2e-6, "fixed": 1e-12}
 
 requires_gpu = pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")
 

@@ -33,7 +33,7 @@ def header_functions():
     with open(os.path.join(ROOT, "include", "ptdr.h")) as f:
         text = f.read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(ptdr_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(ptdr_[a-z0-9_]+)\s*\(", text)))
 
 
 def test_every_declared_symbol_is_exported(lib):
@@ -93,11 +93,17 @@ def test_workspace_sizes(lib):
     assert st == OK and 0 < b <= 128 << 20
     assert ws_size(lib, 0, 14, C128, C64, _lib.PREC_FP32) == (OK, 0)
     assert ws_size(lib, 0, 12, C64, C64, _lib.PREC_SPLIT_BF16_TC)[0] == UNSUPPORTED
-    assert ws_size(lib, 0, 14, C64, C64, _lib.PREC_SPLIT_FP16_TC)[0] == UNSUPPORTED
+    assert ws_size(lib, 0, 14, C64, C64, 4)[0] == INVALID  # no precision 4
     assert ws_size(lib, 0, 15, C64, C64, _lib.PREC_FP32) == (OK, 0)  # intermediate in C
     st, b = ws_size(lib, 0, 14, C64, C64, _lib.PREC_FP64)  # FP64 intermediate, C64 out
     assert st == OK and b > 0
     assert ws_size(lib, 0, 14, C64, C128, _lib.PREC_FP64) == (OK, 0)
+    # fixed point: a 256-byte header (exponent word), plus one L2-sized chunk of
+    # 32-byte intermediate rows once a row no longer fits one tile (n >= 13)
+    assert ws_size(lib, 0, 12, C64, C128, _lib.PREC_FIXED_I128) == (OK, 256)
+    assert ws_size(lib, 1, 10, C128, C128, _lib.PREC_FIXED_I128) == (OK, 256)
+    assert ws_size(lib, 0, 14, C64, C128, _lib.PREC_FIXED_I128) == (OK, 256 + (64 << 20))
+    assert ws_size(lib, 1, 15, C128, C64, _lib.PREC_FIXED_I128) == (OK, 256 + (64 << 20))
     st, b = ws_size(lib, 1, 15, C64, C64, _lib.PREC_FP32)  # compose multi-pass
     assert st == OK and b > 0
     assert ws_size(lib, 0, 0, C64, C64, _lib.PREC_FP32)[0] == INVALID

@@ -22,13 +22,15 @@ def ref_full(A):
     return oracle.direct(A) if n <= 8 else oracle.fwht(A)
 
 
-@pytest.mark.parametrize("n", range(1, 12))
+@pytest.mark.parametrize("n", range(1, 14))
 @pytest.mark.parametrize("prec,adt", [("fp64", np.complex128), ("fp32", np.complex64),
                                       ("fp64", np.complex64), ("fp32", np.complex128)])
 def test_all_sizes(n, prec, adt):
     A = workloads.dense(n, 1000 + n, dtype=adt)
     C = host(ptdr.decompose(dev(A), precision=prec))
-    assert rel_err(C, ref_full(A)) <= TOL[prec]
+    err = rel_err(C, ref_full(A))
+    print(f"decompose n={n} {prec} {np.dtype(adt).name}: rel err {err:.3e}")
+    assert err <= TOL[prec]
     assert ptdr.last_device_status() == 0
 
 
@@ -101,12 +103,52 @@ def test_n14_fp64_into_c64_workspace_path(a14, ref14):
     assert rel_err(C, ref14) <= 1e-6  # rounded to complex64 once at the end
 
 
+def chunked_rel_err(got_rows, ref_rows, N, chunk=2048):
+    """rel_err over all masks, computed chunk by chunk (host memory stays bounded):
+    got_rows(x0, x1) and ref_rows(x0, x1) return rows x0 .. x1 - 1."""
+    num = den = 0.0
+    for x0 in range(0, N, chunk):
+        g = got_rows(x0, x0 + chunk).astype(np.complex128)
+        r = ref_rows(x0, x0 + chunk)
+        num = max(num, float(np.max(np.abs(g - r))))
+        den = max(den, float(np.max(np.abs(r))))
+    return num / den
+
+
 def test_n15_fp32_multipass():
+    """dense n = 15 (rows longer than one tile: first pass + strided HBM passes): the
+    whole output against the oracle's FWHT check, mask chunk by mask chunk, plus sampled
+    rows against the direct trace."""
+    N = 1 << 15
     A = workloads.dense_c64_direct(15, 15)
     C = host(ptdr.decompose(dev(A), precision="fp32"))
-    xs = workloads.sample_masks(15, 15, count=16)
-    ref = oracle.fwht(A, xs=xs)
-    assert rel_err(C[xs.astype(np.int64)], ref) <= TOL["fp32"]
+    xs = workloads.sample_masks(15, 15, count=4)
+    assert rel_err(C[xs.astype(np.int64)], oracle.direct(A, xs=xs)) <= TOL["fp32"]
+    A = A.astype(np.complex128)  # converted once for every chunk of the check
+    err = chunked_rel_err(lambda a, b: C[a:b], lambda a, b: oracle.fwht(A, xs=np.arange(a, b)), N)
+    print(f"decompose n=15 fp32 full output: rel err {err:.3e}")
+    assert err <= TOL["fp32"]
+    assert ptdr.last_device_status() == 0
+
+
+def test_compose_n15_against_oracle():
+    """n = 15 compose (multi-pass), complex64 coefficients fed to both sides, against the
+    oracle's inverse FWHT: every XOR-diagonal of the result, mask chunk by mask chunk."""
+    N = 1 << 15
+    Cq = workloads.dense_c64_direct(15, 151)
+    B = host(ptdr.compose(dev(Cq), precision="fp32"))
+    k = np.arange(N)
+
+    def got(a, b):
+        return np.stack([B[k ^ x, k] for x in range(a, b)])
+
+    def ref(a, b):
+        return oracle.compose_fwht(Cq[a:b], xs=np.arange(a, b))
+
+    err = chunked_rel_err(got, ref, N)
+    print(f"compose n=15 fp32: rel err {err:.3e}")
+    assert err <= TOL["fp32"]
+    assert ptdr.last_device_status() == 0
 
 
 @pytest.mark.parametrize("n", [1, 3, 6, 9, 12])
@@ -117,7 +159,9 @@ def test_round_trip(n, prec):
     Ad = dev(A)
     C = ptdr.decompose(Ad, precision=prec, out_dtype=Ad.dtype)
     B = host(ptdr.compose(C, precision=prec))
-    assert rel_err(B, A) <= TOL[prec] * 4
+    err = rel_err(B, A)
+    print(f"round trip n={n} {prec}: rel err {err:.3e}")
+    assert err <= TOL[prec]
 
 
 @pytest.mark.parametrize("n", [1, 4, 7])
@@ -129,14 +173,35 @@ def test_compose_matches_oracle(n):
         assert rel_err(got, oracle.compose(C, scale=scale)) <= TOL["fp64"]
 
 
+@pytest.mark.parametrize("n", range(1, 14))
+def test_compose_fp32_matches_oracle(n):
+    """FP32 compose (complex64 coefficients fed to both sides) against the oracle's
+    inverse map: the direct O(8^n) sum up to n = 10, the inverse FWHT above."""
+    rng = np.random.default_rng(60 + n)
+    N = 2 ** n
+    C = (rng.standard_normal((N, N)) + 1j * rng.standard_normal((N, N))).astype(np.complex64)
+    for scale in (1.0, 2.0 ** -n):
+        got = host(ptdr.compose(dev(C), scale=scale, precision="fp32"))
+        want = oracle.compose(C, scale=scale) if n <= 10 else oracle.compose_fwht(C, scale=scale)
+        err = rel_err(got, want)
+        print(f"compose n={n} fp32 scale={scale:g}: rel err {err:.3e}")
+        assert err <= TOL["fp32"]
+    assert ptdr.last_device_status() == 0
+
+
 def test_compose_n14_staged(a14, ref14):
     """dense n=14 compose (complex64, FP32): the oracle's coefficients of the seeded
     matrix are mapped back to it, and the adjoint scale 2^-14 scales it exactly."""
-    Cd = dev(ref14.astype(np.complex64))
+    Cq = ref14.astype(np.complex64)
+    Cd = dev(Cq)
+    want = oracle.compose_fwht(Cq)  # the same complex64 coefficients on both sides
     B = host(ptdr.compose(Cd, precision="fp32"))
-    assert rel_err(B, a14) <= 4 * TOL["fp32"]
+    err = rel_err(B, want)
+    print(f"compose n=14 staged fp32: rel err {err:.3e} vs oracle, {rel_err(B, a14):.3e} vs A")
+    assert err <= TOL["fp32"]
+    assert rel_err(B, a14) <= TOL["fp32"]
     Bs = host(ptdr.compose(Cd, scale=2.0 ** -14, precision="fp32"))
-    assert rel_err(Bs * 2.0 ** 14, a14) <= 4 * TOL["fp32"]
+    assert rel_err(Bs * 2.0 ** 14, want) <= TOL["fp32"]
     assert ptdr.last_device_status() == 0
 
 
@@ -144,7 +209,9 @@ def test_compose_n14_round_trip_and_linearity(a14):
     Ad = dev(a14)
     C = ptdr.decompose(Ad, precision="fp32")
     B = host(ptdr.compose(C, precision="fp32"))
-    assert rel_err(B, a14) <= 4 * TOL["fp32"]
+    err = rel_err(B, a14)
+    print(f"round trip n=14 fp32: rel err {err:.3e}")
+    assert err <= TOL["fp32"]
     # single Pauli operators X..X (x = all ones, z = 0) and Z..Z (x = 0, z = all ones)
     Cs = torch.zeros((1 << 14, 1 << 14), dtype=torch.complex64, device="cuda")
     Cs[(1 << 14) - 1, 0] = 1.0
@@ -181,15 +248,6 @@ def test_decompose_host_single_pageable():
     ptdr.decompose_host([torch.from_numpy(A)], hc, precision="fp32")
     torch.cuda.synchronize()
     assert rel_err(hc[0].numpy(), oracle.direct(A)) <= TOL["fp32"]
-
-
-def test_compose_multipass_n15():
-    rng = np.random.default_rng(15)
-    A = workloads.dense_c64_direct(15, 150)
-    Ad = dev(A)
-    C = ptdr.decompose(Ad, precision="fp32")
-    B = host(ptdr.compose(C, precision="fp32"))
-    assert rel_err(B, A) <= 4 * TOL["fp32"]
 
 
 def test_single_operator_inputs_exact():

@@ -215,6 +215,31 @@ def test_compose_against_numpy_kron(n):
     assert rel_err(oracle.compose(C, scale=0.25), 0.25 * ref) < 1e-14
 
 
+@pytest.mark.parametrize("n", [1, 2, 5, 8, 10])
+def test_compose_fwht_matches_direct_compose(n):
+    """The FWHT inverse (large-n compose check) against the direct O(8^n) sum,
+    itself pinned to numpy.kron above; both scales."""
+    rng = np.random.default_rng(40 + n)
+    C = rng.standard_normal((2 ** n, 2 ** n)) + 1j * rng.standard_normal((2 ** n, 2 ** n))
+    for scale in (1.0, 2.0 ** -n):
+        assert rel_err(oracle.compose_fwht(C, scale=scale), oracle.compose(C, scale=scale)) < 1e-13
+
+
+def test_compose_fwht_round_trip_and_single_operator():
+    """compose_fwht inverts fwht (n = 11) and maps a unit coefficient to its operator."""
+    A = rand_c(11, 77)
+    c = oracle.fwht(A)
+    assert rel_err(oracle.compose_fwht(c), A) < 1e-13
+    xs = np.array([0, 5, 2047], np.uint64)  # the XOR-diagonal form for a few masks
+    k = np.arange(2048)
+    want = np.stack([A[k ^ int(x), k] for x in xs])
+    assert rel_err(oracle.compose_fwht(c[xs.astype(np.int64)], xs=xs), want) < 1e-13
+    C = np.zeros((8, 8), complex)
+    x, z = label_masks("YXZ")
+    C[x, z] = 1.0
+    assert np.array_equal(oracle.compose_fwht(C), kron_op("YXZ"))
+
+
 def test_linearity():
     n = 6
     A, B = rand_c(n, 1), rand_c(n, 2)

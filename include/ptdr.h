@@ -95,12 +95,17 @@ typedef enum {
  * Defines: c_P = 2^-n tr(P A) for every P in P_n (Sec. II.A; the paper's
  * Algorithm 1 computes the same set by walking the Pauli tree, Sec. III.A).
  *
- *   A, a_type   device, 4^n elements of a_type in {C64, C128}, row-major.
- *   C, c_type   device, 4^n elements of c_type in {C64, C128}; C[x*2^n + z].
+ *   A, a_type   device, 4^n elements of a_type, row-major: C64, C128, or a
+ *               real matrix (F32, F64).
+ *   C, c_type   device, 4^n elements of c_type; C[x*2^n + z].  C64 / C128
+ *               store c_P; a real type (F32 / F64) stores Re c_P only, which
+ *               for a Hermitian A is all of c_P (Thm 2: Hermitian matrices
+ *               have real coefficients) -- the Hermitian real-output mode,
+ *               half the write bytes of a complex output.
  *   n           1 <= n <= 15.
  *   prec        FP64: any a_type/c_type.  FP32: any a_type/c_type (C128 input
  *               is rounded to float32 on load).  SPLIT_BF16_TC: n = 14,
- *               a_type = c_type = C64, with A, C and the workspace 32-byte
+ *               a_type = C64, c_type = C64 or F32, with A, C and the workspace 32-byte
  *               aligned (PTDR_ERR_INVALID_ARG otherwise); other n or types
  *               return PTDR_ERR_UNSUPPORTED.  FIXED_I128: any a_type/c_type
  *               (a non-finite input entry is recorded as PTDR_ERR_INVALID_ARG
@@ -120,7 +125,8 @@ ptdr_status ptdr_decompose(const void* A, ptdr_dtype a_type, void* C, ptdr_dtype
  * adjoint of ptdr_decompose (D(A)_P = 2^-n <P, A>), which is the backward
  * pass of the decomposition for automatic differentiation.
  *
- *   C, c_type   device, 4^n coefficients, c_type in {C64, C128}.
+ *   C, c_type   device, 4^n coefficients: C64, C128, or real coefficients
+ *               (F32, F64), which describe a Hermitian A (Thm 2).
  *   A, a_type   device output, 4^n elements, a_type in {C64, C128}.
  *   n, prec, workspace, stream as for ptdr_decompose (SPLIT_BF16_TC unsupported;
  *               FIXED_I128 applies a power-of-two scale exactly and any
@@ -271,6 +277,61 @@ ptdr_status ptdr_decompose_host_scratch_size(int n, ptdr_dtype a_type, ptdr_dtyp
  * the kernels wrote since the previous call (PTDR_OK if none) and clears it.
  */
 ptdr_status ptdr_last_device_status(void* stream);
+
+/*
+ * Decomposition algebra (Sec. IV.B, "Combinations of matrices"): the
+ * decomposition of a matrix built from others, computed from their
+ * coefficient arrays (layout C[x*2^n + z]) without decomposing it again.
+ * Device pointers; asynchronous on `stream`; the library allocates nothing.
+ */
+
+/*
+ * ptdr_coeff_lincomb -- linear combination (Sec. IV.B.3): the coefficients of
+ * mu A + B are mu alpha_j + beta_j.  C_out = mu * CA + CB elementwise.
+ *   n          1 <= n <= 15 (4^n coefficients per array).
+ *   mu_re, mu_im  the complex factor mu (real arrays need mu_im = 0:
+ *              PTDR_ERR_UNSUPPORTED otherwise).
+ *   CA, CB     device inputs of c_type; CB may be NULL (C_out = mu CA).
+ *   C_out      device output of c_type; may be CB itself (in place), must not
+ *              otherwise overlap an input.
+ *   c_type     C64, C128 (computed in float32 / float64), F32, F64.
+ */
+ptdr_status ptdr_coeff_lincomb(int n, double mu_re, double mu_im, const void* CA, const void* CB,
+                               void* C_out, ptdr_dtype c_type, void* stream);
+
+/*
+ * ptdr_coeff_block_diag -- direct sum and block-diagonal matrices (Sec.
+ * IV.B.1-2).  The block-diagonal matrix diag(A_0, ..., A_{2^m - 1}) of 2^m
+ * blocks of n qubits is sum_i |i><i| (x) A_i, and |i><i| =
+ * 2^-m sum_t (-1)^{|t & i|} Z^t on the top m qubits, so its n + m qubit
+ * coefficients are
+ *     C_out[x][z + 2^n t] = 2^-m sum_i (-1)^{|t & i|} C_i[x][z]   (x < 2^n),
+ * and 0 for every mask x >= 2^n (no X or Y on a top qubit).  m = 1 is the
+ * direct sum A (+) B = I (x) (A + B)/2 + Z (x) (A - B)/2; larger block
+ * counts follow by applying it to groups (the paper's recursive pairing).
+ *   n, m       n >= 1, 1 <= m <= 4, n + m <= 15.
+ *   h_blocks   HOST array of 2^m device pointers: block i's coefficients (4^n
+ *              of c_type), block i sits at rows/columns [i 2^n, (i+1) 2^n).
+ *   C_out      device output, 4^(n+m) coefficients of c_type, 16-byte aligned,
+ *              not overlapping a block.
+ */
+ptdr_status ptdr_coeff_block_diag(int n, int m, const void* const* h_blocks, void* C_out,
+                                  ptdr_dtype c_type, void* stream);
+
+/*
+ * ptdr_coeff_hermitian_augment -- Hermitian matrix augmentation (Sec.
+ * IV.B.5): [[0, A^H], [A, 0]] = X (x) sum Re(alpha_j) P_j + Y (x) sum
+ * Im(alpha_j) P_j, so on n + 1 qubits
+ *     C_out[x + 2^n][z] = Re CA[x][z],   C_out[x + 2^n][z + 2^n] = Im CA[x][z],
+ * and every other coefficient is 0.  All are real (the augmented matrix is
+ * Hermitian, Thm 2); at most twice as many nonzero terms as A has.
+ *   CA, a_type      device, 4^n coefficients (C64, C128; F32/F64 = real).
+ *   C_out, out_type device, 4^(n+1) coefficients, 16-byte aligned: real
+ *                   (F32, F64) or complex (C64, C128, zero imaginary parts).
+ *   n               1 <= n <= 14.
+ */
+ptdr_status ptdr_coeff_hermitian_augment(int n, const void* CA, ptdr_dtype a_type, void* C_out,
+                                         ptdr_dtype out_type, void* stream);
 
 /*
  * ptdr_probe_fp64_adds -- measurement helper, not part of the method (the

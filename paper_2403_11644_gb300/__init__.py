@@ -10,14 +10,17 @@ from .ptdr import (  # noqa: F401
     PRECISIONS,
     BatchedPlan,
     PtdrDecompose,
+    block_diag,
     compose,
     decompose,
     decompose_autograd,
     decompose_batched,
     decompose_host,
     decompose_structured,
+    hermitian_augment,
     host_scratch_size,
     last_device_status,
+    lincomb,
     structured_masks,
     workspace_size,
 )

@@ -46,6 +46,9 @@ SIGNATURES = {
     "ptdr_decompose_host_scratch_size": [_i, _i, _i, _i, _szp],
     "ptdr_last_device_status": [_vp],
     "ptdr_probe_fp64_adds": [_vp, _i, _i, _i, ctypes.POINTER(ctypes.c_double), _vp],
+    "ptdr_coeff_lincomb": [_i, _d, _d, _vp, _vp, _vp, _i, _vp],
+    "ptdr_coeff_block_diag": [_i, _i, _vp, _vp, _i, _vp],
+    "ptdr_coeff_hermitian_augment": [_i, _vp, _i, _vp, _i, _vp],
     "ptdr_status_string": [_i],
     "ptdr_version": [],
 }

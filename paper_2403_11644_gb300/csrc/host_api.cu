@@ -60,8 +60,7 @@ ptdr_status host_layout(int n, ptdr_dtype a_t, ptdr_dtype c_t, ptdr_precision pr
     if ((int)a_t < PTDR_C64 || (int)a_t > PTDR_F64 || (int)c_t < PTDR_C64 || (int)c_t > PTDR_F64)
         return PTDR_ERR_INVALID_ARG;
     if ((int)prec < PTDR_PREC_FP64 || (int)prec > PTDR_PREC_FIXED_I128) return PTDR_ERR_INVALID_ARG;
-    if (!dtype_complex(a_t) || !dtype_complex(c_t)) return PTDR_ERR_UNSUPPORTED;
-    if (prec == PTDR_PREC_SPLIT_BF16_TC && (a_t != PTDR_C64 || c_t != PTDR_C64))
+    if (prec == PTDR_PREC_SPLIT_BF16_TC && (a_t != PTDR_C64 || (c_t != PTDR_C64 && c_t != PTDR_F32)))
         return PTDR_ERR_UNSUPPORTED;
     ptdr_status v = make_dense_plan(false, n, a_t, c_t, prec, plan);
     if (v != PTDR_OK) return v;

@@ -68,6 +68,15 @@ template <> struct in_of<double2> {
     static constexpr int bias = 1023;
     __device__ static __forceinline__ fx2 cvt(double2 v, int S) { return fx2{fixed_of(v.x, S), fixed_of(v.y, S)}; }
 };
+// real inputs (a real matrix, or real coefficients of a Hermitian matrix)
+template <> struct in_of<float> {
+    static constexpr int bias = 127;
+    __device__ static __forceinline__ fx2 cvt(float v, int S) { return fx2{fixed_of(v, S), 0}; }
+};
+template <> struct in_of<double> {
+    static constexpr int bias = 1023;
+    __device__ static __forceinline__ fx2 cvt(double v, int S) { return fx2{fixed_of(v, S), 0}; }
+};
 
 // How the fixed-point results become output values: value = X 2^(q_pow - S),
 // times `mul` when the scale is not a power of two.
@@ -107,6 +116,25 @@ template <> struct out_of<float2> {
         re ^= (uint32_t)((p >> 1) & 1) << 31;
         im ^= (uint32_t)((p ^ (p >> 1)) & 1) << 31;
         return make_float2(__uint_as_float(re), __uint_as_float(im));
+    }
+};
+
+// Real outputs store the real part of (-i)^p X 2^q (Hermitian A: all of c, Thm 2):
+// Re for even p, Im for odd p, negated for p = 2, 3.
+template <> struct out_of<double> {
+    __device__ static __forceinline__ double cvt(fx2 v, int p, const FxOut& o)
+    {
+        uint64_t re = f64_bits((p & 1) ? v.y : v.x, o.q) ^ ((uint64_t)((p >> 1) & 1) << 63);
+        double r = __longlong_as_double((long long)re);
+        return o.use_mul ? r * o.mul : r;
+    }
+};
+template <> struct out_of<float> {
+    __device__ static __forceinline__ float cvt(fx2 v, int p, const FxOut& o)
+    {
+        if (o.use_mul) return (float)out_of<double>::cvt(v, p, o);
+        const uint32_t re = f32_bits((p & 1) ? v.y : v.x, o.q) ^ ((uint32_t)((p >> 1) & 1) << 31);
+        return __uint_as_float(re);
     }
 };
 
@@ -379,19 +407,52 @@ cudaError_t run_fx_strided(const FxLaunch& p, unsigned int* st, cudaStream_t s)
     return cudaGetLastError();
 }
 
-// Dispatch on (input type, output type) for a given load/store pair.
+// Dispatch on (input type, output type) for a given load/store pair.  The
+// intermediate rows (Store::RowBuf) ignore the output type.
+template <typename InT, Load LD, Store ST>
+cudaError_t fx_tile_out(const FxLaunch& p, ptdr_dtype out_t, unsigned int* st, cudaStream_t s)
+{
+    if (ST == Store::RowBuf) return run_fx_tile<InT, float2, LD, ST>(p, st, s);
+    switch (out_t) {
+    case PTDR_C64: return run_fx_tile<InT, float2, LD, ST>(p, st, s);
+    case PTDR_C128: return run_fx_tile<InT, double2, LD, ST>(p, st, s);
+    case PTDR_F32:
+        if constexpr (ST == Store::RowPhaseOut) return run_fx_tile<InT, float, LD, ST>(p, st, s);
+        break;
+    case PTDR_F64:
+        if constexpr (ST == Store::RowPhaseOut) return run_fx_tile<InT, double, LD, ST>(p, st, s);
+        break;
+    }
+    return cudaErrorInvalidValue;
+}
+
 template <Load LD, Store ST>
 cudaError_t fx_tile_types(const FxLaunch& p, ptdr_dtype in_t, ptdr_dtype out_t, unsigned int* st, cudaStream_t s)
 {
-    const bool i64 = in_t == PTDR_C128, o64 = out_t == PTDR_C128;
-    if (i64) return o64 ? run_fx_tile<double2, double2, LD, ST>(p, st, s) : run_fx_tile<double2, float2, LD, ST>(p, st, s);
-    return o64 ? run_fx_tile<float2, double2, LD, ST>(p, st, s) : run_fx_tile<float2, float2, LD, ST>(p, st, s);
+    switch (in_t) {
+    case PTDR_C64: return fx_tile_out<float2, LD, ST>(p, out_t, st, s);
+    case PTDR_C128: return fx_tile_out<double2, LD, ST>(p, out_t, st, s);
+    case PTDR_F32: return fx_tile_out<float, LD, ST>(p, out_t, st, s);
+    case PTDR_F64: return fx_tile_out<double, LD, ST>(p, out_t, st, s);
+    }
+    return cudaErrorInvalidValue;
 }
 
 template <Store ST>
 cudaError_t fx_strided_types(const FxLaunch& p, ptdr_dtype out_t, unsigned int* st, cudaStream_t s)
 {
-    return out_t == PTDR_C128 ? run_fx_strided<double2, ST>(p, st, s) : run_fx_strided<float2, ST>(p, st, s);
+    if (ST == Store::RowBuf) return run_fx_strided<float2, ST>(p, st, s);
+    switch (out_t) {
+    case PTDR_C64: return run_fx_strided<float2, ST>(p, st, s);
+    case PTDR_C128: return run_fx_strided<double2, ST>(p, st, s);
+    case PTDR_F32:
+        if constexpr (ST == Store::RowPhaseOut) return run_fx_strided<float, ST>(p, st, s);
+        break;
+    case PTDR_F64:
+        if constexpr (ST == Store::RowPhaseOut) return run_fx_strided<double, ST>(p, st, s);
+        break;
+    }
+    return cudaErrorInvalidValue;
 }
 
 } // namespace
@@ -408,12 +469,12 @@ cudaError_t launch_fixed(const DensePlan& plan, const void* in, void* out, void*
     int* emax = (int*)ws;
     cudaError_t e = cudaMemsetAsync(ws, 0, fixed_ws_header(), s);
     if (e != cudaSuccess) return e;
-    const bool in64 = plan.in_t == PTDR_C128;
+    const bool in64 = plan.in_t == PTDR_C128 || plan.in_t == PTDR_F64;
     {
         int dev = 0, sms = 0;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
         if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        const uint64_t words = 2 * N * N;
+        const uint64_t words = (dtype_complex(plan.in_t) ? 2 : 1) * N * N;
         const unsigned grid = (unsigned)std::min<uint64_t>((uint64_t)sms * 8, std::max<uint64_t>(1, words / 256));
         if (in64)
             k_fx_maxexp<uint64_t><<<grid, 256, 0, s>>>((const uint64_t*)in, words, emax, st);

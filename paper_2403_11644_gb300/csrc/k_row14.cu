@@ -52,6 +52,9 @@ template <> __device__ __forceinline__ float2 ld_in<double2>(const double2* p)
     double2 v = __ldg(p);
     return make_float2((float)v.x, (float)v.y);
 }
+// a real matrix enters with a zero imaginary part
+template <> __device__ __forceinline__ float2 ld_in<float>(const float* p) { return make_float2(__ldg(p), 0.f); }
+template <> __device__ __forceinline__ float2 ld_in<double>(const double* p) { return make_float2((float)__ldg(p), 0.f); }
 
 template <typename OutT>
 __device__ __forceinline__ void st_out(OutT* p, float2 v);
@@ -60,6 +63,9 @@ template <> __device__ __forceinline__ void st_out<double2>(double2* p, float2 v
 {
     __stcs(p, make_double2((double)v.x, (double)v.y));
 }
+// real outputs store the real part (Hermitian A: all of c, Thm 2)
+template <> __device__ __forceinline__ void st_out<float>(float* p, float2 v) { __stcs(p, v.x); }
+template <> __device__ __forceinline__ void st_out<double>(double* p, float2 v) { __stcs(p, (double)v.x); }
 
 } // namespace
 
@@ -129,10 +135,22 @@ static cudaError_t run_row14(const void* A, void* C, unsigned int* st, cudaStrea
 cudaError_t launch_row14(const void* A, ptdr_dtype a_t, void* C, ptdr_dtype c_t, unsigned int* st,
                          cudaStream_t s)
 {
-    if (a_t == PTDR_C64 && c_t == PTDR_C64) return run_row14<float2, float2>(A, C, st, s);
-    if (a_t == PTDR_C64 && c_t == PTDR_C128) return run_row14<float2, double2>(A, C, st, s);
-    if (a_t == PTDR_C128 && c_t == PTDR_C64) return run_row14<double2, float2>(A, C, st, s);
-    if (a_t == PTDR_C128 && c_t == PTDR_C128) return run_row14<double2, double2>(A, C, st, s);
+    auto by_out = [&](auto in_tag) -> cudaError_t {
+        using InT = decltype(in_tag);
+        switch (c_t) {
+        case PTDR_C64: return run_row14<InT, float2>(A, C, st, s);
+        case PTDR_C128: return run_row14<InT, double2>(A, C, st, s);
+        case PTDR_F32: return run_row14<InT, float>(A, C, st, s);
+        case PTDR_F64: return run_row14<InT, double>(A, C, st, s);
+        }
+        return cudaErrorInvalidValue;
+    };
+    switch (a_t) {
+    case PTDR_C64: return by_out(float2{});
+    case PTDR_C128: return by_out(double2{});
+    case PTDR_F32: return by_out(float{});
+    case PTDR_F64: return by_out(double{});
+    }
     return cudaErrorInvalidValue;
 }
 

@@ -151,9 +151,11 @@ static cudaError_t tile_by_store(const TileLaunch& p, unsigned int* st, cudaStre
     using T2 = cplx_t<T>;
     switch (p.store) {
     case Store::RowBuf: return run_tile<T, InT, T2, LD, Store::RowBuf>(p, st, s);
-    case Store::RowPhaseOut:
+    case Store::RowPhaseOut: // a real output type stores the real part (Hermitian A: all of c, Thm 2)
         if (p.dst_t == PTDR_C64) return run_tile<T, InT, float2, LD, Store::RowPhaseOut>(p, st, s);
         if (p.dst_t == PTDR_C128) return run_tile<T, InT, double2, LD, Store::RowPhaseOut>(p, st, s);
+        if (p.dst_t == PTDR_F32) return run_tile<T, InT, float, LD, Store::RowPhaseOut>(p, st, s);
+        if (p.dst_t == PTDR_F64) return run_tile<T, InT, double, LD, Store::RowPhaseOut>(p, st, s);
         break;
     case Store::ScatterA:
         if (p.dst_t == PTDR_C64) return run_tile<T, InT, float2, LD, Store::ScatterA>(p, st, s);
@@ -169,13 +171,17 @@ static cudaError_t tile_by_load(const TileLaunch& p, unsigned int* st, cudaStrea
     using T2 = cplx_t<T>;
     switch (p.load) {
     case Load::RowBuf: return tile_by_store<T, T2, Load::RowBuf>(p, st, s);
-    case Load::GatherA:
+    case Load::GatherA: // real matrices enter with a zero imaginary part
         if (p.src_t == PTDR_C64) return tile_by_store<T, float2, Load::GatherA>(p, st, s);
         if (p.src_t == PTDR_C128) return tile_by_store<T, double2, Load::GatherA>(p, st, s);
+        if (p.src_t == PTDR_F32) return tile_by_store<T, float, Load::GatherA>(p, st, s);
+        if (p.src_t == PTDR_F64) return tile_by_store<T, double, Load::GatherA>(p, st, s);
         break;
-    case Load::RowPhaseC:
+    case Load::RowPhaseC: // real coefficients: a Hermitian matrix (Thm 2)
         if (p.src_t == PTDR_C64) return tile_by_store<T, float2, Load::RowPhaseC>(p, st, s);
         if (p.src_t == PTDR_C128) return tile_by_store<T, double2, Load::RowPhaseC>(p, st, s);
+        if (p.src_t == PTDR_F32) return tile_by_store<T, float, Load::RowPhaseC>(p, st, s);
+        if (p.src_t == PTDR_F64) return tile_by_store<T, double, Load::RowPhaseC>(p, st, s);
         break;
     }
     return cudaErrorInvalidValue;
@@ -196,6 +202,8 @@ static cudaError_t strided_by_store(const StridedLaunch& p, unsigned int* st, cu
     case Store::RowPhaseOut:
         if (p.dst_t == PTDR_C64) return run_strided<T, float2, Store::RowPhaseOut>(p, st, s);
         if (p.dst_t == PTDR_C128) return run_strided<T, double2, Store::RowPhaseOut>(p, st, s);
+        if (p.dst_t == PTDR_F32) return run_strided<T, float, Store::RowPhaseOut>(p, st, s);
+        if (p.dst_t == PTDR_F64) return run_strided<T, double, Store::RowPhaseOut>(p, st, s);
         break;
     case Store::ScatterA:
         if (p.dst_t == PTDR_C64) return run_strided<T, float2, Store::ScatterA>(p, st, s);

@@ -305,8 +305,11 @@ struct TcPipeTables {
     float2* stage; // kSlots x 128 rows x 2^14
 };
 
+// kRealOut: C holds float32 real parts only (the Hermitian real-output mode:
+// for Hermitian A every coefficient is real, Thm 2), half the write bytes.
+template <bool kRealOut>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_tc14_pipe(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmS, float2* __restrict__ C,
+    k_tc14_pipe(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmS, void* __restrict__ Cv,
                 TcPipeTables tab, unsigned int* st)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -662,7 +665,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                     w2 ^= w1 & pb;
                     w1 ^= pb;
                 }
-                float2* out = C + ((uint64_t)x << kLog) + (uint64_t)(kT * 64 * hcol) + (uint64_t)zl;
+                const uint64_t o0 = ((uint64_t)x << kLog) + (uint64_t)(kT * 64 * hcol) + (uint64_t)zl;
+                float2* out = (float2*)Cv + o0;
+                float* outr = (float*)Cv + o0;
 #pragma unroll
                 for (int cc = 0; cc < 2; ++cc) {
                     const uint32_t bs = (uint32_t)__popc(xt & (64 * hcol + 32 * cc)) & 3u;
@@ -683,8 +688,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const bool o = ((odd >> u) & 1u) != 0;
                         const uint32_t ox = (o ? vi[u] : vr[u]) ^ sgn(sx, u);
                         const uint32_t oy = (o ? vr[u] : vi[u]) ^ sgn(sy, u);
-                        if (in_bounds(st, ((uint64_t)x << kLog) + (uint64_t)(kT * (64 * hcol + 32 * cc + u) + zl), lim))
-                            __stcs(out + (size_t)(kT * (32 * cc + u)), make_float2(__uint_as_float(ox), __uint_as_float(oy)));
+                        if (in_bounds(st, ((uint64_t)x << kLog) + (uint64_t)(kT * (64 * hcol + 32 * cc + u) + zl), lim)) {
+                            if constexpr (kRealOut)
+                                __stcs(outr + (size_t)(kT * (32 * cc + u)), __uint_as_float(ox));
+                            else
+                                __stcs(out + (size_t)(kT * (32 * cc + u)), make_float2(__uint_as_float(ox), __uint_as_float(oy)));
+                        }
                     }
                 }
             }
@@ -858,11 +867,12 @@ bool encode_boxes(CUtensorMap* m, const void* base, uint64_t rows, uint64_t cols
 
 } // namespace
 
-cudaError_t launch_tc14_pipe(const void* A, void* C, void* ws, unsigned int* st, cudaStream_t s)
+cudaError_t launch_tc14_pipe(const void* A, void* C, bool real_out, void* ws, unsigned int* st, cudaStream_t s)
 {
     static std::mutex mu;
     static int grid_for[128];
-    cudaError_t e = cudaFuncSetAttribute(k_tc14_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+    auto kern = real_out ? k_tc14_pipe<true> : k_tc14_pipe<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
     if (e != cudaSuccess) return e;
     int dev = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
@@ -888,7 +898,7 @@ cudaError_t launch_tc14_pipe(const void* A, void* C, void* ws, unsigned int* st,
     if (!encode_boxes(&tmA, A, kN, 2 * kN) || !encode_boxes(&tmS, tab.stage, (uint64_t)kSlots * kT * kT, 2 * kT))
         return cudaErrorInvalidValue;
     if ((e = cudaMemsetAsync(ws, 0, 4096, s)) != cudaSuccess) return e;
-    k_tc14_pipe<<<grid, kThreads, kSmemBytes, s>>>(tmA, tmS, (float2*)C, tab, st);
+    kern<<<grid, kThreads, kSmemBytes, s>>>(tmA, tmS, C, tab, st);
     return cudaGetLastError();
 }
 

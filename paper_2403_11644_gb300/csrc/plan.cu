@@ -65,8 +65,9 @@ ptdr_status make_dense_plan(bool compose, int n, ptdr_dtype in_t, ptdr_dtype out
         return PTDR_OK;
     }
     if (prec == PTDR_PREC_SPLIT_BF16_TC) {
-        // the tensor-core path covers the n = 14 complex64 workload
-        if (compose || n != 14 || in_t != PTDR_C64 || out_t != PTDR_C64) return PTDR_ERR_UNSUPPORTED;
+        // the tensor-core path covers the n = 14 complex64 workload (complex64
+        // coefficients, or float32 real parts in the Hermitian real-output mode)
+        if (compose || n != 14 || in_t != PTDR_C64 || (out_t != PTDR_C64 && out_t != PTDR_F32)) return PTDR_ERR_UNSUPPORTED;
         DensePlan p;
         p.compose = false;
         p.n = n;
@@ -160,7 +161,7 @@ ptdr_status execute_dense(const DensePlan& p, const void* in, void* out, void* w
     if (p.kernel == DenseKernel::Tc14) {
         // 32-byte vector loads and stores of A, C and the staging rows
         if ((uintptr_t)in % 32 || (uintptr_t)out % 32 || (uintptr_t)ws % 32) return PTDR_ERR_INVALID_ARG;
-        e = launch_tc14_pipe(in, out, ws, st, s);
+        e = launch_tc14_pipe(in, out, p.out_t == PTDR_F32, ws, st, s);
         return e == cudaSuccess ? PTDR_OK : PTDR_ERR_CUDA;
     }
     if (p.kernel == DenseKernel::Compose14) {

@@ -61,7 +61,7 @@ cudaError_t launch_row14(const void* A, ptdr_dtype a_t, void* C, ptdr_dtype c_t,
                          unsigned int* status, cudaStream_t s);
 cudaError_t launch_dense14_staged(const void* A, void* C, void* ws, unsigned int* status, cudaStream_t s);
 size_t dense14_staged_workspace();
-cudaError_t launch_tc14_pipe(const void* A, void* C, void* ws, unsigned int* status, cudaStream_t s);
+cudaError_t launch_tc14_pipe(const void* A, void* C, bool real_out, void* ws, unsigned int* status, cudaStream_t s);
 size_t tc14_pipe_workspace();
 cudaError_t launch_compose14_staged(const void* C, void* A, double scale, void* ws, unsigned int* status,
                                     cudaStream_t s);

@@ -90,10 +90,12 @@ ptdr_status validate_dense(const void* in, ptdr_dtype in_t, const void* out, ptd
     if (!in || !out) return PTDR_ERR_INVALID_ARG;
     if (n < 1 || n > kMaxDenseN) return PTDR_ERR_INVALID_ARG;
     if (!valid_dtype(in_t) || !valid_dtype(out_t) || !valid_prec(prec)) return PTDR_ERR_INVALID_ARG;
-    if (!dtype_complex(in_t) || !dtype_complex(out_t)) return PTDR_ERR_UNSUPPORTED;
+    // decompose: real or complex A; a real C stores Re c (all of c for Hermitian A, Thm 2).
+    // compose: real coefficients describe a Hermitian A, which is complex.
+    if (compose && !dtype_complex(out_t)) return PTDR_ERR_UNSUPPORTED;
     if (prec == PTDR_PREC_SPLIT_BF16_TC) {
         if (compose) return PTDR_ERR_UNSUPPORTED;
-        if (in_t != PTDR_C64 || out_t != PTDR_C64) return PTDR_ERR_UNSUPPORTED;
+        if (in_t != PTDR_C64 || (out_t != PTDR_C64 && out_t != PTDR_F32)) return PTDR_ERR_UNSUPPORTED;
     }
     const size_t elems = (size_t)1 << (2 * n);
     if ((uintptr_t)in % dtype_bytes(in_t) || (uintptr_t)out % dtype_bytes(out_t))

@@ -91,8 +91,8 @@ def compose(C: torch.Tensor, scale: float = 1.0, precision: str = "fp32", out_dt
     """A = scale * sum_P C[P] P (the inverse of decompose for scale = 1)."""
     C = _cuda(C, "C")
     n = _n_of(C.shape[0])
-    if out_dtype is None:
-        out_dtype = C.dtype
+    if out_dtype is None:  # real coefficients describe a Hermitian, complex A (Thm 2)
+        out_dtype = {torch.float32: torch.complex64, torch.float64: torch.complex128}.get(C.dtype, C.dtype)
     A = out if out is not None else torch.empty((1 << n, 1 << n), dtype=out_dtype, device=C.device)
     ws_bytes = workspace_size("compose", n, A.dtype, C.dtype, precision)
     ws = _workspace(ws_bytes, C.device) if ws_bytes else None
@@ -185,6 +185,65 @@ def decompose_structured(bands: torch.Tensor, s: int, masks=None, precision: str
         _dtype_code(C.dtype), _prec(precision),
         ctypes.c_void_p(ws.data_ptr() if ws is not None else 0), wsz.value, _stream(bands.device)),
         "ptdr_decompose_structured")
+    return C
+
+
+# ----------------------------------------------------------- decomposition algebra
+
+
+def _coeff_n(C: torch.Tensor, name: str) -> int:
+    if C.ndim != 2 or C.shape[0] != C.shape[1]:
+        raise ValueError(f"{name} must be a square 2^n x 2^n coefficient array")
+    return _n_of(C.shape[0])
+
+
+def lincomb(mu, CA: torch.Tensor, CB: torch.Tensor = None, out=None) -> torch.Tensor:
+    """Coefficients of mu A + B from those of A and B (Sec. IV.B.3): mu * CA + CB."""
+    CA = _cuda(CA, "CA")
+    n = _coeff_n(CA, "CA")
+    if CB is not None:
+        CB = _cuda(CB, "CB")
+        if CB.shape != CA.shape or CB.dtype != CA.dtype:
+            raise ValueError("CA and CB must have the same shape and dtype")
+    C = out if out is not None else torch.empty_like(CA)
+    mu = complex(mu)
+    check(_lib.load().ptdr_coeff_lincomb(
+        n, mu.real, mu.imag, ctypes.c_void_p(CA.data_ptr()),
+        ctypes.c_void_p(CB.data_ptr() if CB is not None else 0), ctypes.c_void_p(C.data_ptr()),
+        _dtype_code(CA.dtype), _stream(CA.device)), "ptdr_coeff_lincomb")
+    return C
+
+
+def block_diag(blocks, out=None) -> torch.Tensor:
+    """Coefficients of diag(A_0, ..., A_{2^m-1}) from those of the 2^m blocks
+    (Sec. IV.B.1-2; two blocks = the direct sum A (+) B)."""
+    blocks = [_cuda(b, "block") for b in blocks]
+    k = len(blocks)
+    if k < 2 or k & (k - 1):
+        raise ValueError("need 2^m blocks, m >= 1")
+    m = k.bit_length() - 1
+    n = _coeff_n(blocks[0], "block")
+    for b in blocks:
+        if b.shape != blocks[0].shape or b.dtype != blocks[0].dtype:
+            raise ValueError("blocks must have the same shape and dtype")
+    C = out if out is not None else torch.empty((1 << (n + m), 1 << (n + m)), dtype=blocks[0].dtype,
+                                                device=blocks[0].device)
+    ptrs = (ctypes.c_void_p * k)(*[b.data_ptr() for b in blocks])
+    check(_lib.load().ptdr_coeff_block_diag(n, m, ctypes.cast(ptrs, ctypes.c_void_p), ctypes.c_void_p(C.data_ptr()),
+                                            _dtype_code(C.dtype), _stream(C.device)), "ptdr_coeff_block_diag")
+    return C
+
+
+def hermitian_augment(CA: torch.Tensor, out_dtype=None, out=None) -> torch.Tensor:
+    """Coefficients of [[0, A^H], [A, 0]] (n + 1 qubits) from those of A (Sec. IV.B.5)."""
+    CA = _cuda(CA, "CA")
+    n = _coeff_n(CA, "CA")
+    if out_dtype is None:
+        out_dtype = torch.float64 if CA.dtype in (torch.complex128, torch.float64) else torch.float32
+    C = out if out is not None else torch.empty((2 << n, 2 << n), dtype=out_dtype, device=CA.device)
+    check(_lib.load().ptdr_coeff_hermitian_augment(
+        n, ctypes.c_void_p(CA.data_ptr()), _dtype_code(CA.dtype), ctypes.c_void_p(C.data_ptr()),
+        _dtype_code(C.dtype), _stream(CA.device)), "ptdr_coeff_hermitian_augment")
     return C
 
 

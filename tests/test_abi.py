@@ -130,8 +130,20 @@ def test_decompose_argument_errors(lib):
     assert decompose(lib, FAKE_A, C64, FAKE_C, C64, 16, P32) == INVALID
     assert decompose(lib, FAKE_A, 9, FAKE_C, C64, 4, P32) == INVALID
     assert decompose(lib, FAKE_A, C64, FAKE_C, C64, 4, 9) == INVALID
-    assert decompose(lib, FAKE_A, _lib.F32, FAKE_C, C64, 4, P32) == UNSUPPORTED
+    # real matrices and real (Hermitian-mode) outputs pass validation; the fake
+    # pointers then fail the device check (GPU) or there is no device (CPU)
+    ND = INVALID if HAVE_GPU else NO_DEVICE
+    assert decompose(lib, FAKE_A, _lib.F32, FAKE_C, C64, 4, P32) == ND
+    assert decompose(lib, FAKE_A, C64, FAKE_C, _lib.F64, 4, P32) == ND
     assert decompose(lib, FAKE_A, C128, FAKE_C, C64, 4, TC) == UNSUPPORTED
+    assert decompose(lib, FAKE_A, C64, FAKE_C, _lib.F64, 14, TC) == UNSUPPORTED  # TC real output is F32
+    # compose: real coefficients in (Hermitian A), but never a real A out
+    st = lib.ptdr_compose(ctypes.c_void_p(FAKE_C), _lib.F32, ctypes.c_void_p(FAKE_A), C64, 4, 1.0, P32,
+                          None, 0, None)
+    assert st == ND
+    st = lib.ptdr_compose(ctypes.c_void_p(FAKE_C), C64, ctypes.c_void_p(FAKE_A), _lib.F32, 4, 1.0, P32,
+                          None, 0, None)
+    assert st == UNSUPPORTED
     assert decompose(lib, FAKE_A + 4, C64, FAKE_C, C64, 4, P32) == INVALID  # misaligned
     assert decompose(lib, FAKE_A, C64, FAKE_A + 64, C64, 4, P32) == INVALID  # overlap
     # FP64 arithmetic into a complex64 output at n = 14 needs a workspace
@@ -198,7 +210,7 @@ def test_host_entry_point_argument_errors(lib):
     assert lib.ptdr_decompose_host_scratch_size(10, C64, C64, P32, ctypes.byref(sz)) == OK
     assert sz.value >= 4 * (8 << 20)  # two input and two output buffers of 2^20 complex64
     assert lib.ptdr_decompose_host_scratch_size(16, C64, C64, P32, ctypes.byref(sz)) == INVALID
-    assert lib.ptdr_decompose_host_scratch_size(10, _lib.F32, C64, P32, ctypes.byref(sz)) == UNSUPPORTED
+    assert lib.ptdr_decompose_host_scratch_size(10, _lib.F32, C64, P32, ctypes.byref(sz)) == OK  # real matrix
     host_a = np.zeros((2, 16, 16), np.complex64)
     host_c = np.zeros((2, 16, 16), np.complex64)
     ha = (ctypes.c_void_p * 2)(host_a[0].ctypes.data, host_a[1].ctypes.data)

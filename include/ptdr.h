@@ -189,6 +189,35 @@ ptdr_status ptdr_structured_workspace_size(int n, int s, const uint64_t* h_masks
                                            ptdr_precision prec, size_t* bytes);
 
 /*
+ * Anti-band matrices (Remark 1 of Sec. IV.A: for anti-diagonal matrices the
+ * roles of I, Z and of X, Y swap).  A is anti-band of half-width s when
+ * A[r][c] = 0 unless |r + c - (2^n - 1)| <= s (s = 0: anti-diagonal).  Then
+ * B = A J, J = X (x) ... (x) X the exchange matrix, is band-diagonal, and the
+ * anti-band storage is B's band storage:
+ *        antibands[(d + s) * 2^n + c] = A[c + d][2^n - 1 - c],  d in [-s, s].
+ * The reachable masks are the band's masks XOR (2^n - 1) (anti-diagonal: the
+ * single mask x = 2^n - 1, only X and Y on every qubit), and the coefficient
+ * of mask x_A is (-1)^{|z|} (-i)^{|x_A & z|} 2^-n WHT(d_{x_A ^ (2^n - 1)})[z]
+ * over B's gathered diagonal.
+ *
+ * ptdr_antistructured_masks -- as ptdr_structured_masks, for anti-band masks
+ *   (ascending).  Host only.
+ * ptdr_decompose_antistructured -- as ptdr_decompose_structured, with the
+ *   anti-band storage above and anti-band masks in h_masks; row i of C holds
+ *   mask h_masks[i].  A real output type stores the real part (all of c when
+ *   A is Hermitian, Thm 2).
+ * ptdr_antistructured_workspace_size -- its workspace bytes.  Host only.
+ */
+ptdr_status ptdr_antistructured_masks(int n, int s, uint64_t* h_masks, size_t* count);
+ptdr_status ptdr_decompose_antistructured(const void* antibands, ptdr_dtype b_type, int n, int s,
+                                          const uint64_t* h_masks, size_t n_masks, void* C,
+                                          ptdr_dtype c_type, ptdr_precision prec, void* workspace,
+                                          size_t workspace_bytes, void* stream);
+ptdr_status ptdr_antistructured_workspace_size(int n, int s, const uint64_t* h_masks, size_t n_masks,
+                                               ptdr_dtype b_type, ptdr_dtype c_type,
+                                               ptdr_precision prec, size_t* bytes);
+
+/*
  * ptdr_decompose_batched -- decomposes `count` independent matrices of
  * possibly different sizes in one persistent launch (the paper's forest of
  * independent subtrees, Sec. V.B, taken across matrices).
@@ -332,6 +361,37 @@ ptdr_status ptdr_coeff_block_diag(int n, int m, const void* const* h_blocks, voi
  */
 ptdr_status ptdr_coeff_hermitian_augment(int n, const void* CA, ptdr_dtype a_type, void* C_out,
                                          ptdr_dtype out_type, void* stream);
+
+/*
+ * ptdr_coeff_select -- the sparse form of a decomposition that a block-encoding
+ * by a linear combination of unitaries needs (Sec. VI, "Block-encoding using
+ * Pauli decomposition"): the kept terms P_i, their coefficients alpha_i and
+ * the normaliser sum_i |alpha_i| of the ancilla state
+ * sum_i sqrt(|alpha_i|) |i> / sqrt(sum_i |alpha_i|).
+ * Keeps every coefficient with |c_P| > threshold; with k > 0, only the k
+ * largest of those (ties in magnitude go to the lower index x*2^n + z).
+ * Magnitudes are compared in float32 for complex64/float32 arrays and as
+ * |c|^2 in float64 for complex128 (so complex128 values below about 1e-154
+ * count as zero); float64 arrays compare |v|.
+ *   n            1 <= n <= 15; C holds 4^n coefficients of c_type (any type).
+ *   threshold    finite, >= 0 (0 keeps every nonzero coefficient).
+ *   k            0 = no count limit.
+ *   d_idx, d_val device outputs, capacity `cap` each: kept indices x*2^n + z
+ *                (uint64, ascending) and their coefficients (c_type).  Only the
+ *                first `cap` kept terms are written; cap = 0 (NULL outputs)
+ *                just counts.
+ *   d_count      device uint64: number of kept terms (may exceed cap).
+ *   d_l1         device double: sum of |c_P| over every kept term.
+ *   workspace    device, 256-byte aligned, ptdr_select_workspace_size() bytes.
+ * The output order, count and normaliser are deterministic run to run.
+ */
+ptdr_status ptdr_coeff_select(int n, const void* C, ptdr_dtype c_type, double threshold,
+                              unsigned long long k, uint64_t* d_idx, void* d_val, size_t cap,
+                              unsigned long long* d_count, double* d_l1, void* workspace,
+                              size_t workspace_bytes, void* stream);
+
+/* Workspace bytes for ptdr_coeff_select.  Host only. */
+ptdr_status ptdr_select_workspace_size(size_t* bytes);
 
 /*
  * ptdr_probe_fp64_adds -- measurement helper, not part of the method (the

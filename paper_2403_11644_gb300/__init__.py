@@ -21,6 +21,7 @@ from .ptdr import (  # noqa: F401
     host_scratch_size,
     last_device_status,
     lincomb,
+    select,
     structured_masks,
     workspace_size,
 )

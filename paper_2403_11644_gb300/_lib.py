@@ -39,6 +39,9 @@ SIGNATURES = {
     "ptdr_structured_masks": [_i, _i, _vp, _szp],
     "ptdr_decompose_structured": [_vp, _i, _i, _i, _vp, _sz, _vp, _i, _i, _vp, _sz, _vp],
     "ptdr_structured_workspace_size": [_i, _i, _vp, _sz, _i, _i, _i, _szp],
+    "ptdr_antistructured_masks": [_i, _i, _vp, _szp],
+    "ptdr_decompose_antistructured": [_vp, _i, _i, _i, _vp, _sz, _vp, _i, _i, _vp, _sz, _vp],
+    "ptdr_antistructured_workspace_size": [_i, _i, _vp, _sz, _i, _i, _i, _szp],
     "ptdr_decompose_batched": [_vp, _vp, _vp, _vp, _i, _i, _i, _i, _vp, _sz, _vp],
     "ptdr_batched_workspace_size": [_vp, _i, _i, _i, _i, _szp],
     "ptdr_decompose_batched_static": [_vp, _vp, _vp, _vp, _i, _i, _i, _i, _vp],
@@ -49,6 +52,8 @@ SIGNATURES = {
     "ptdr_coeff_lincomb": [_i, _d, _d, _vp, _vp, _vp, _i, _vp],
     "ptdr_coeff_block_diag": [_i, _i, _vp, _vp, _i, _vp],
     "ptdr_coeff_hermitian_augment": [_i, _vp, _i, _vp, _i, _vp],
+    "ptdr_coeff_select": [_i, _vp, _i, _d, ctypes.c_ulonglong, _vp, _vp, _sz, _vp, _vp, _vp, _sz, _vp],
+    "ptdr_select_workspace_size": [_szp],
     "ptdr_status_string": [_i],
     "ptdr_version": [],
 }

@@ -40,11 +40,21 @@ def _deps():
         os.path.join(HERE, "..", "include", "ptdr.h"), os.path.abspath(__file__)]
 
 
+def _stamp(lib: str) -> str:
+    return lib + ".sources"
+
+
+def _source_list() -> str:
+    return "\n".join(os.path.basename(s) for s in _sources())
+
+
 def build(checked: bool = False, force: bool = False, verbose: bool = False) -> str:
     lib = lib_path(checked)
-    if not force and os.path.exists(lib):
+    if not force and os.path.exists(lib) and os.path.exists(_stamp(lib)):
         t = os.path.getmtime(lib)
-        if all(os.path.getmtime(d) <= t for d in _deps()):
+        with open(_stamp(lib)) as f:
+            same_sources = f.read() == _source_list()  # a source added or removed also rebuilds
+        if same_sources and all(os.path.getmtime(d) <= t for d in _deps()):
             return lib
     os.makedirs(OUT, exist_ok=True)
     tag = "checked" if checked else "release"
@@ -70,6 +80,8 @@ def build(checked: bool = False, force: bool = False, verbose: bool = False) -> 
     subprocess.check_call([cc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "shared",
                            "-Xlinker", "-rpath,/usr/local/cuda/lib64"])
     os.replace(tmp, lib)
+    with open(_stamp(lib), "w") as f:
+        f.write(_source_list())
     if verbose:
         print(lib)
     return lib

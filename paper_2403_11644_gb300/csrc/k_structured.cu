@@ -168,7 +168,11 @@ __global__ void __launch_bounds__(256) k_band_expand(BandMaskLaunch p, unsigned 
             if (j == 0) acc = neg_if(w, neg);
             else acc = neg ? csub(acc, w) : cadd(acc, w);
         }
-        const cplx_t<T> c = phase_flip(as_cplx(acc), __popcll(p.x & z));
+        // band: (-i)^{|x&z|}; anti-band, A = B J with J = X..X: the coefficient of
+        // the anti-band mask x_A = x ^ (2^n - 1) is (-1)^{|z|} (-i)^{|x_A & z|} times the
+        // same transform value, i.e. the exponent |x_A & z| + 2 |z|
+        const int ph = p.anti ? __popcll(p.anti_x & z) + 2 * __popcll(z) : __popcll(p.x & z);
+        const cplx_t<T> c = phase_flip(as_cplx(acc), ph);
         const uint64_t gi = p.out_row * N + z;
         if (in_bounds(st, gi, p.out_elems)) io<OutT>::st((OutT*)p.out + gi, c);
     }

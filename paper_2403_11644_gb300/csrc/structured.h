@@ -22,6 +22,8 @@ struct BandMaskLaunch {
     uint64_t t[kMaxBandPairs];
     int64_t d[kMaxBandPairs]; // x - 2 t: the band each pair reads
     bool real;    // real band: V rows hold real values
+    bool anti;    // anti-band: the storage is the band matrix B = A J and x = x_A ^ (2^n - 1)
+    uint64_t anti_x; // the anti-band mask x_A (phase (-1)^{|z|} (-i)^{|x_A & z|})
     void* ws;     // V rows, npairs x 2^f compute-type values (complex, or real for a real band)
     uint64_t ws_elems;
     void* out;    // output array

@@ -208,10 +208,12 @@ ptdr_status ptdr_structured_workspace_size(int n, int s, const uint64_t* h_masks
     return PTDR_OK;
 }
 
-ptdr_status ptdr_decompose_structured(const void* bands, ptdr_dtype b_type, int n, int s,
-                                      const uint64_t* h_masks, size_t n_masks, void* C,
-                                      ptdr_dtype c_type, ptdr_precision prec, void* workspace,
-                                      size_t workspace_bytes, void* stream)
+// The band path for band storage and masks h_masks; with anti_masks the
+// storage is that of B = A J (an anti-band A) and h_masks[i] = anti_masks[i] ^
+// (2^n - 1), and row i receives the coefficients of A's mask anti_masks[i].
+static ptdr_status decompose_band(const void* bands, ptdr_dtype b_type, int n, int s, const uint64_t* h_masks,
+                                  size_t n_masks, void* C, ptdr_dtype c_type, ptdr_precision prec, void* workspace,
+                                  size_t workspace_bytes, void* stream, const uint64_t* anti_masks)
 {
     if (!C) return PTDR_ERR_INVALID_ARG;
     ptdr_status v = validate_structured(bands, b_type, n, s, h_masks, n_masks, c_type, prec);
@@ -270,6 +272,8 @@ ptdr_status ptdr_decompose_structured(const void* bands, ptdr_dtype b_type, int 
         p.c_t = c_type;
         p.calc = calc;
         p.real = real;
+        p.anti = anti_masks != nullptr;
+        p.anti_x = anti_masks ? anti_masks[i] : 0;
         p.n = n;
         p.s = s;
         p.x = m.x;
@@ -327,6 +331,61 @@ ptdr_status ptdr_decompose_structured(const void* bands, ptdr_dtype b_type, int 
             if (!ok && e == cudaSuccess) e = cudaErrorUnknown;
         }
     return e == cudaSuccess ? PTDR_OK : PTDR_ERR_CUDA;
+}
+
+ptdr_status ptdr_decompose_structured(const void* bands, ptdr_dtype b_type, int n, int s,
+                                      const uint64_t* h_masks, size_t n_masks, void* C,
+                                      ptdr_dtype c_type, ptdr_precision prec, void* workspace,
+                                      size_t workspace_bytes, void* stream)
+{
+    return decompose_band(bands, b_type, n, s, h_masks, n_masks, C, c_type, prec, workspace, workspace_bytes,
+                          stream, nullptr);
+}
+
+// Anti-band matrices (Remark 1 of Sec. IV.A: I and Z swap roles with X and Y):
+// A J is a band matrix for J = X (x) ... (x) X, so the masks are the band's
+// masks XOR (2^n - 1).
+ptdr_status ptdr_antistructured_masks(int n, int s, uint64_t* h_masks, size_t* count)
+{
+    ptdr_status v = ptdr_structured_masks(n, s, h_masks, count);
+    if (v != PTDR_OK || !h_masks) return v;
+    const uint64_t all = (1ull << n) - 1;
+    for (size_t i = 0; i < *count; ++i) h_masks[i] ^= all;
+    std::sort(h_masks, h_masks + *count);
+    return PTDR_OK;
+}
+
+static ptdr_status band_masks_of(int n, const uint64_t* h_masks, size_t n_masks, std::vector<uint64_t>* out)
+{
+    if (!h_masks || n < 1 || n > 30) return PTDR_ERR_INVALID_ARG;
+    const uint64_t all = (1ull << n) - 1;
+    out->resize(n_masks);
+    for (size_t i = 0; i < n_masks; ++i) {
+        if (h_masks[i] > all) return PTDR_ERR_INVALID_ARG;
+        (*out)[i] = h_masks[i] ^ all;
+    }
+    return PTDR_OK;
+}
+
+ptdr_status ptdr_antistructured_workspace_size(int n, int s, const uint64_t* h_masks, size_t n_masks,
+                                               ptdr_dtype b_type, ptdr_dtype c_type, ptdr_precision prec,
+                                               size_t* bytes)
+{
+    std::vector<uint64_t> xb;
+    ptdr_status v = band_masks_of(n, h_masks, n_masks, &xb);
+    if (v != PTDR_OK) return v;
+    return ptdr_structured_workspace_size(n, s, xb.data(), n_masks, b_type, c_type, prec, bytes);
+}
+
+ptdr_status ptdr_decompose_antistructured(const void* antibands, ptdr_dtype b_type, int n, int s,
+                                          const uint64_t* h_masks, size_t n_masks, void* C, ptdr_dtype c_type,
+                                          ptdr_precision prec, void* workspace, size_t workspace_bytes, void* stream)
+{
+    std::vector<uint64_t> xb;
+    ptdr_status v = band_masks_of(n, h_masks, n_masks, &xb);
+    if (v != PTDR_OK) return v;
+    return decompose_band(antibands, b_type, n, s, xb.data(), n_masks, C, c_type, prec, workspace, workspace_bytes,
+                          stream, h_masks);
 }
 
 } // extern "C"

@@ -145,41 +145,47 @@ def decompose_host(As, Cs, precision: str = "fp32", device=None, scratch=None):
     return Cs
 
 
-def structured_masks(n: int, s: int) -> np.ndarray:
-    """Masks reachable by a band matrix of half-width s (host computation)."""
+def structured_masks(n: int, s: int, anti: bool = False) -> np.ndarray:
+    """Masks reachable by a band matrix of half-width s (host computation); with
+    anti=True, by an anti-band matrix (the band's masks XOR 2^n - 1)."""
     lib = _lib.load()
+    fn = lib.ptdr_antistructured_masks if anti else lib.ptdr_structured_masks
     cnt = ctypes.c_size_t(0)
-    check(lib.ptdr_structured_masks(n, s, None, ctypes.byref(cnt)), "ptdr_structured_masks")
+    check(fn(n, s, None, ctypes.byref(cnt)), "ptdr_structured_masks")
     out = np.zeros(cnt.value, np.uint64)
-    check(lib.ptdr_structured_masks(n, s, out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(cnt)),
-          "ptdr_structured_masks")
+    check(fn(n, s, out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(cnt)), "ptdr_structured_masks")
     return out
 
 
 def decompose_structured(bands: torch.Tensor, s: int, masks=None, precision: str = "fp64",
-                         out_dtype=None, workspace=None, out=None) -> torch.Tensor:
+                         out_dtype=None, workspace=None, out=None, anti: bool = False) -> torch.Tensor:
     """Coefficients of a band matrix on its reachable masks (rows follow ``masks``).
 
-    ``bands`` has shape (2s+1, 2^n) with bands[d+s, c] = A[c+d, c].
+    ``bands`` has shape (2s+1, 2^n) with bands[d+s, c] = A[c+d, c].  With anti=True
+    A is anti-band and bands[d+s, c] = A[c+d, 2^n-1-c] (Remark 1 of Sec. IV.A).
     """
     bands = _cuda(bands, "bands")
     if bands.ndim != 2 or bands.shape[0] != 2 * s + 1:
         raise ValueError("bands must have shape (2s+1, 2^n)")
     n = _n_of(bands.shape[1])
-    h_masks = structured_masks(n, s) if masks is None else np.ascontiguousarray(masks, np.uint64)
+    h_masks = structured_masks(n, s, anti) if masks is None else np.ascontiguousarray(masks, np.uint64)
     if out_dtype is None:
-        out_dtype = bands.dtype if not bands.dtype.is_complex else (
-            torch.complex128 if precision == "fp64" else torch.complex64)
+        if anti:  # anti-band coefficients are complex even for real storage
+            out_dtype = torch.complex128 if precision == "fp64" else torch.complex64
+        else:
+            out_dtype = bands.dtype if not bands.dtype.is_complex else (
+                torch.complex128 if precision == "fp64" else torch.complex64)
     C = out if out is not None else torch.empty((len(h_masks), 1 << n), dtype=out_dtype,
                                                 device=bands.device)
     lib = _lib.load()
     hp = h_masks.ctypes.data_as(ctypes.c_void_p)
     wsz = ctypes.c_size_t(0)
-    check(lib.ptdr_structured_workspace_size(n, s, hp, len(h_masks), _dtype_code(bands.dtype),
-                                             _dtype_code(C.dtype), _prec(precision),
-                                             ctypes.byref(wsz)), "ptdr_structured_workspace_size")
+    size_fn = lib.ptdr_antistructured_workspace_size if anti else lib.ptdr_structured_workspace_size
+    check(size_fn(n, s, hp, len(h_masks), _dtype_code(bands.dtype), _dtype_code(C.dtype), _prec(precision),
+                  ctypes.byref(wsz)), "ptdr_structured_workspace_size")
     ws = workspace if workspace is not None else (_workspace(wsz.value, bands.device) if wsz.value else None)
-    check(lib.ptdr_decompose_structured(
+    run_fn = lib.ptdr_decompose_antistructured if anti else lib.ptdr_decompose_structured
+    check(run_fn(
         ctypes.c_void_p(bands.data_ptr()), _dtype_code(bands.dtype), n, s,
         hp, len(h_masks), ctypes.c_void_p(C.data_ptr()),
         _dtype_code(C.dtype), _prec(precision),
@@ -245,6 +251,42 @@ def hermitian_augment(CA: torch.Tensor, out_dtype=None, out=None) -> torch.Tenso
         n, ctypes.c_void_p(CA.data_ptr()), _dtype_code(CA.dtype), ctypes.c_void_p(C.data_ptr()),
         _dtype_code(C.dtype), _stream(CA.device)), "ptdr_coeff_hermitian_augment")
     return C
+
+
+def select(C: torch.Tensor, threshold: float = 0.0, k: int = 0):
+    """Sparse form of a decomposition for an LCU block-encoding (Sec. VI).
+
+    Returns (indices, values, l1): the indices x * 2^n + z (ascending, int64) of the
+    coefficients with |c| > threshold (the k largest of them when k > 0; ties go to the
+    lower index), their values, and the normaliser sum |alpha_i| over them.  With no
+    k the count is read back first (one synchronisation) to size the outputs."""
+    C = _cuda(C, "C")
+    n = _coeff_n(C, "C")
+    lib = _lib.load()
+    wsz = ctypes.c_size_t(0)
+    check(lib.ptdr_select_workspace_size(ctypes.byref(wsz)), "ptdr_select_workspace_size")
+    ws = _workspace(wsz.value, C.device)
+    cnt = torch.zeros(1, dtype=torch.int64, device=C.device)
+    l1 = torch.zeros(1, dtype=torch.float64, device=C.device)
+
+    def run(cap, idx, val):
+        check(lib.ptdr_coeff_select(
+            n, ctypes.c_void_p(C.data_ptr()), _dtype_code(C.dtype), float(threshold), int(k),
+            ctypes.c_void_p(idx.data_ptr() if idx is not None else 0),
+            ctypes.c_void_p(val.data_ptr() if val is not None else 0), cap,
+            ctypes.c_void_p(cnt.data_ptr()), ctypes.c_void_p(l1.data_ptr()),
+            ctypes.c_void_p(ws.data_ptr()), wsz.value, _stream(C.device)), "ptdr_coeff_select")
+
+    if k > 0:
+        cap = min(int(k), C.numel())
+    else:
+        run(0, None, None)
+        cap = int(cnt.item())
+    idx = torch.empty(max(cap, 1), dtype=torch.int64, device=C.device)
+    val = torch.empty(max(cap, 1), dtype=C.dtype, device=C.device)
+    run(cap, idx, val)
+    m = int(cnt.item())
+    return idx[:m], val[:m], float(l1.item())
 
 
 class BatchedPlan:

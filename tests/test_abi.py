@@ -273,3 +273,45 @@ def test_structured_workspace_covers_concurrent_masks(lib):
     assert st == OK and max(each) < b <= sum((v + 255) // 256 * 256 for v in each)
     st, b = ws(10, 3, [int(m) for m in oracle.band_masks(10, 3)], _lib.C128, _lib.PREC_FP64)
     assert st == OK and b > 0
+
+
+@pytest.mark.parametrize("n,s", [(1, 0), (3, 0), (4, 1), (5, 2), (6, 3), (6, 5)])
+def test_antistructured_masks_brute_force(lib, n, s):
+    """Anti-band masks (Remark 1 of Sec. IV.A) against a brute-force enumeration of the
+    XOR r ^ c over every entry with |r + c - (2^n - 1)| <= s."""
+    N = 1 << n
+    want = sorted({r ^ c for r in range(N) for c in range(N) if abs(r + c - (N - 1)) <= s})
+    cnt = ctypes.c_size_t(0)
+    assert lib.ptdr_antistructured_masks(n, s, None, ctypes.byref(cnt)) == OK
+    out = np.zeros(cnt.value, np.uint64)
+    assert lib.ptdr_antistructured_masks(n, s, out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(cnt)) == OK
+    assert out.tolist() == want
+    if s == 0:
+        assert want == [N - 1]  # anti-diagonal: X or Y on every qubit
+
+
+def test_select_and_algebra_argument_errors(lib):
+    sz = ctypes.c_size_t(0)
+    assert lib.ptdr_select_workspace_size(ctypes.byref(sz)) == OK and sz.value > 0
+    st = lib.ptdr_coeff_select(4, ctypes.c_void_p(FAKE_C), _lib.C64, -1.0, 0, None, None, 0,
+                               ctypes.c_void_p(FAKE_A), ctypes.c_void_p(FAKE_A + 8), ctypes.c_void_p(FAKE_A + 4096),
+                               sz.value, None)
+    assert st == INVALID  # negative threshold
+    st = lib.ptdr_coeff_select(4, ctypes.c_void_p(FAKE_C), _lib.C64, 0.0, 0, None, None, 10,
+                               ctypes.c_void_p(FAKE_A), ctypes.c_void_p(FAKE_A + 8), ctypes.c_void_p(FAKE_A + 4096),
+                               sz.value, None)
+    assert st == INVALID  # capacity without output arrays
+    st = lib.ptdr_coeff_select(4, ctypes.c_void_p(FAKE_C), _lib.C64, 0.0, 0, None, None, 0,
+                               ctypes.c_void_p(FAKE_A), ctypes.c_void_p(FAKE_A + 8), None, 0, None)
+    assert st == WORKSPACE
+    assert lib.ptdr_coeff_lincomb(4, 1.0, 2.0, ctypes.c_void_p(FAKE_A), None, ctypes.c_void_p(FAKE_C), _lib.F64,
+                                  None) == UNSUPPORTED  # a complex factor on real arrays
+    assert lib.ptdr_coeff_lincomb(4, float("inf"), 0.0, ctypes.c_void_p(FAKE_A), None, ctypes.c_void_p(FAKE_C),
+                                  _lib.C64, None) == INVALID
+    blocks = (ctypes.c_void_p * 2)(FAKE_A, FAKE_A + (1 << 20))
+    assert lib.ptdr_coeff_block_diag(4, 0, ctypes.cast(blocks, ctypes.c_void_p), ctypes.c_void_p(FAKE_C), _lib.C64,
+                                     None) == INVALID  # m = 0
+    assert lib.ptdr_coeff_block_diag(14, 2, ctypes.cast(blocks, ctypes.c_void_p), ctypes.c_void_p(FAKE_C), _lib.C64,
+                                     None) == INVALID  # n + m > 15
+    assert lib.ptdr_coeff_hermitian_augment(15, ctypes.c_void_p(FAKE_A), _lib.C64, ctypes.c_void_p(FAKE_C), _lib.F32,
+                                            None) == INVALID

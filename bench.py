@@ -630,19 +630,29 @@ def main():
                 C2 = torch.empty(C.shape, dtype=od, device=dev)
                 wsb = ptdr.workspace_size("decompose", N_QUBITS, A.dtype, od, p2)
                 ws2 = torch.empty(max(wsb, 1), dtype=torch.uint8, device=dev)
-                for _ in range(2):
-                    ptdr.decompose(A, precision=p2, out=C2, workspace=ws2)
-                torch.cuda.synchronize(dev)
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                reps = 3
-                a.record(stream)
-                for _ in range(reps):
-                    ptdr.decompose(A, precision=p2, out=C2, workspace=ws2)
-                b.record(stream)
-                torch.cuda.synchronize(dev)
-                ms = a.elapsed_time(b) / reps
+                def time_path():
+                    for _ in range(2):
+                        ptdr.decompose(A, precision=p2, out=C2, workspace=ws2)
+                    torch.cuda.synchronize(dev)
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    reps = 3
+                    a.record(stream)
+                    for _ in range(reps):
+                        ptdr.decompose(A, precision=p2, out=C2, workspace=ws2)
+                    b.record(stream)
+                    torch.cuda.synchronize(dev)
+                    return a.elapsed_time(b) / reps
+                ms = time_path()
                 extra[p2] = {"coeffs_per_s": ncoef / (ms * 1e-3), "ms": ms,
                              "algorithmic_gbs": (in_b + C2.element_size() * C2.numel()) / ms / 1e6}
+                if p2 == "fp64":
+                    # its rows (256 KiB) take a first pass and strided HBM passes: autotune
+                    # their schedule on these buffers, then time the tuned plan
+                    tuned = ptdr.autotune("decompose", A, C2, p2, workspace=ws2)
+                    ms_t = time_path()
+                    extra[p2].update({"ms_default_schedule": ms, "ms": ms_t, "schedule": tuned,
+                                      "coeffs_per_s": ncoef / (ms_t * 1e-3),
+                                      "algorithmic_gbs": (in_b + C2.element_size() * C2.numel()) / ms_t / 1e6})
                 acc_rows[p2] = C2[xs_t].cpu().numpy()
                 del C2, ws2
             except Exception as e:  # report, never hide

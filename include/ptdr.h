@@ -258,8 +258,9 @@ ptdr_status ptdr_batched_workspace_size(const int* h_n, int count, ptdr_dtype a_
  *   count      at most 4096 matrices; larger batches return
  *              PTDR_ERR_WORKSPACE (use ptdr_decompose_batched instead).
  *   The first call on each device looks up the array's device address (with
- *   that device current) and caches it; make that first call before any
- *   stream capture.  Every call shares the one array, which keeps the last
+ *   that device current) and caches it for the life of the process; make that
+ *   first call before any stream capture, and do not use the library across a
+ *   cudaDeviceReset (which reloads the array at a new address).  Every call shares the one array, which keeps the last
  *   call's tables; each call rewrites all of it (including the work-queue
  *   counter) before use, so results never depend on an earlier call, but two
  *   calls whose work overlaps on the GPU (different streams, or different
@@ -300,6 +301,50 @@ ptdr_status ptdr_decompose_host(const void* const* h_A, void* const* h_C, int co
 /* Device scratch bytes for ptdr_decompose_host.  Host only. */
 ptdr_status ptdr_decompose_host_scratch_size(int n, ptdr_dtype a_type, ptdr_dtype c_type,
                                              ptdr_precision prec, size_t* bytes);
+
+/*
+ * Autotuner of the strided HBM passes.  Rows too long for one on-chip tile
+ * (FP64 n >= 14, complex128 input at n = 15, compose n = 15, ...) run as a
+ * first pass over row segments and strided passes over the high bits of the
+ * transform through an intermediate in HBM -- the GPU form of the forest cut
+ * at a level of Sec. V.B.  Their schedule is a tuning choice.
+ */
+typedef struct {
+    int tile_log2;      /* first-pass tile, log2 of its bytes (15..17) */
+    int masks_log2;     /* masks per first-pass tile, log2 (0..3; 0 for compose) */
+    int pass_tile_log2; /* strided-pass tile, log2 bytes: sets the bits per pass */
+    int threads;        /* threads per CTA (256 or 512) */
+    double ms;          /* the measured time of one call with this schedule */
+} ptdr_tune_params;
+
+/*
+ * ptdr_autotune -- times every candidate schedule of the multi-pass plan of
+ * ptdr_decompose (op = PTDR_OP_DECOMPOSE) or ptdr_compose (PTDR_OP_COMPOSE)
+ * for (n, in_type, out_type, prec) with CUDA events on `stream`, on the
+ * caller's buffers (in is read, out and the workspace are overwritten), and
+ * keeps the fastest for this GPU: in memory, and in the JSON file that the
+ * environment variable PTDR_TUNE_CACHE names, if any.  Synchronous (it waits
+ * for its timings).  Later calls of ptdr_decompose / ptdr_compose with the
+ * same GPU, op, n, types and precision run the stored schedule.  Returns
+ * PTDR_ERR_UNSUPPORTED when the plan has no strided passes (rows fit on chip,
+ * or a dedicated kernel runs them); arguments as for ptdr_decompose.
+ */
+ptdr_status ptdr_autotune(ptdr_op op, int n, ptdr_dtype in_type, ptdr_dtype out_type,
+                          ptdr_precision prec, const void* in, void* out, void* workspace,
+                          size_t workspace_bytes, void* stream, ptdr_tune_params* best);
+
+/*
+ * ptdr_tune_lookup / ptdr_tune_store -- host-only access to the tuning cache
+ * (loaded lazily from PTDR_TUNE_CACHE).  The key is the GPU name as
+ * cudaGetDeviceProperties reports it, the op, n, the two types and the
+ * precision.  Lookup returns PTDR_ERR_UNSUPPORTED when the key has no entry;
+ * store replaces the entry and rewrites the file (PTDR_ERR_INVALID_ARG if it
+ * cannot be written).
+ */
+ptdr_status ptdr_tune_lookup(const char* gpu_name, ptdr_op op, int n, ptdr_dtype in_type,
+                             ptdr_dtype out_type, ptdr_precision prec, ptdr_tune_params* out);
+ptdr_status ptdr_tune_store(const char* gpu_name, ptdr_op op, int n, ptdr_dtype in_type,
+                            ptdr_dtype out_type, ptdr_precision prec, const ptdr_tune_params* params);
 
 /*
  * ptdr_last_device_status -- synchronises `stream`, returns the status word

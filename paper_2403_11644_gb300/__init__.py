@@ -10,6 +10,7 @@ from .ptdr import (  # noqa: F401
     PRECISIONS,
     BatchedPlan,
     PtdrDecompose,
+    autotune,
     block_diag,
     compose,
     decompose,

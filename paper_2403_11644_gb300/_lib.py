@@ -54,6 +54,9 @@ SIGNATURES = {
     "ptdr_coeff_hermitian_augment": [_i, _vp, _i, _vp, _i, _vp],
     "ptdr_coeff_select": [_i, _vp, _i, _d, ctypes.c_ulonglong, _vp, _vp, _sz, _vp, _vp, _vp, _sz, _vp],
     "ptdr_select_workspace_size": [_szp],
+    "ptdr_autotune": [_i, _i, _i, _i, _i, _vp, _vp, _vp, _sz, _vp, _vp],
+    "ptdr_tune_lookup": [ctypes.c_char_p, _i, _i, _i, _i, _i, _vp],
+    "ptdr_tune_store": [ctypes.c_char_p, _i, _i, _i, _i, _i, _vp],
     "ptdr_status_string": [_i],
     "ptdr_version": [],
 }

@@ -77,7 +77,7 @@ def build(checked: bool = False, force: bool = False, verbose: bool = False) -> 
     with cf.ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
         objs = list(ex.map(compile_one, _sources()))
     tmp = lib + ".tmp"
-    subprocess.check_call([cc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "shared",
+    subprocess.check_call([cc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "shared", "-ldl",
                            "-Xlinker", "-rpath,/usr/local/cuda/lib64"])
     os.replace(tmp, lib)
     with open(_stamp(lib), "w") as f:

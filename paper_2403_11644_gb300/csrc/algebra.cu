@@ -194,6 +194,7 @@ extern "C" {
 ptdr_status ptdr_coeff_lincomb(int n, double mu_re, double mu_im, const void* CA, const void* CB, void* C_out,
                                ptdr_dtype c_type, void* stream)
 {
+    PTDR_TRACE();
     if (n < 1 || n > kMaxDenseN || !CA || !C_out || !valid_dtype(c_type)) return PTDR_ERR_INVALID_ARG;
     if (!std::isfinite(mu_re) || !std::isfinite(mu_im)) return PTDR_ERR_INVALID_ARG;
     if (!dtype_complex(c_type) && mu_im != 0.0) return PTDR_ERR_UNSUPPORTED; // real arrays stay real
@@ -225,6 +226,7 @@ ptdr_status ptdr_coeff_lincomb(int n, double mu_re, double mu_im, const void* CA
 ptdr_status ptdr_coeff_block_diag(int n, int m, const void* const* h_blocks, void* C_out, ptdr_dtype c_type,
                                   void* stream)
 {
+    PTDR_TRACE();
     if (n < 1 || m < 1 || m > kMaxBlockLog || n + m > kMaxDenseN || !h_blocks || !C_out || !valid_dtype(c_type))
         return PTDR_ERR_INVALID_ARG;
     const uint64_t in_bytes = (1ull << (2 * n)) * dtype_bytes(c_type);
@@ -261,6 +263,7 @@ ptdr_status ptdr_coeff_block_diag(int n, int m, const void* const* h_blocks, voi
 ptdr_status ptdr_coeff_hermitian_augment(int n, const void* CA, ptdr_dtype a_type, void* C_out, ptdr_dtype out_type,
                                          void* stream)
 {
+    PTDR_TRACE();
     if (n < 1 || n + 1 > kMaxDenseN || !CA || !C_out || !valid_dtype(a_type) || !valid_dtype(out_type))
         return PTDR_ERR_INVALID_ARG;
     const uint64_t in_bytes = (1ull << (2 * n)) * dtype_bytes(a_type);

@@ -53,6 +53,7 @@ ptdr_status ptdr_decompose_batched(const void* const* d_A, void* const* d_C, con
                                    ptdr_dtype c_type, ptdr_precision prec, void* workspace,
                                    size_t workspace_bytes, void* stream)
 {
+    PTDR_TRACE();
     if (!d_A || !d_C || !d_n) return PTDR_ERR_INVALID_ARG;
     size_t need = 0;
     long long items = 0;

@@ -25,14 +25,18 @@ constexpr size_t kStaticScratchBytes = 16 + 2 * kTableBytes; // 32,784 bytes
 // rank -> matrix table, then the rank -> first item table.
 static __device__ __align__(256) unsigned char g_batched_scratch[kStaticScratchBytes];
 
+constexpr int kMaxDevices = 128;
 std::mutex g_mu;
-void* g_scratch_addr[128];
+void* g_scratch_addr[kMaxDevices];
 
 // Device address of the scratch array on device `dev` (which must be
 // current).  In host code the array's name is only a host-side stand-in, so
-// the address is looked up once per device and cached.
+// the address is looked up once per device and cached for the life of the
+// process (a cudaDeviceReset reloads the module, so the library must not be
+// used across one).
 ptdr_status scratch_address(int dev, void** out)
 {
+    if (dev < 0 || dev >= kMaxDevices) return PTDR_ERR_NO_DEVICE;
     std::lock_guard<std::mutex> lk(g_mu);
     if (!g_scratch_addr[dev]) {
         void* p = nullptr;
@@ -57,6 +61,7 @@ ptdr_status ptdr_decompose_batched_static(const void* const* d_A, void* const* d
                                           ptdr_dtype a_type, ptdr_dtype c_type,
                                           ptdr_precision prec, void* stream)
 {
+    PTDR_TRACE();
     if (!d_A || !d_C || !d_n) return PTDR_ERR_INVALID_ARG;
     // Same argument rules as ptdr_decompose_batched; the table size it reports
     // must fit the static array.
@@ -64,6 +69,7 @@ ptdr_status ptdr_decompose_batched_static(const void* const* d_A, void* const* d
     ptdr_status v = ptdr_batched_workspace_size(h_n, count, a_type, c_type, prec, &need);
     if (v != PTDR_OK) return v;
     if (count > kStaticMaxMatrices || need > kStaticScratchBytes) return PTDR_ERR_WORKSPACE;
+    if (fault_injected("plan")) return PTDR_ERR_INTERNAL;
     long long items = 0;
     int max_n = 0;
     for (int i = 0; i < count; ++i) {
@@ -82,6 +88,7 @@ ptdr_status ptdr_decompose_batched_static(const void* const* d_A, void* const* d
     void* scratch = nullptr;
     v = scratch_address(dev, &scratch);
     if (v != PTDR_OK) return v;
+    if (fault_injected("launch")) return PTDR_ERR_CUDA;
 
     // Every table entry the kernels read is rewritten by the planner kernel at
     // the start of each call, and the planner also resets the queue head to

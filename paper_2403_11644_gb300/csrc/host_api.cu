@@ -92,6 +92,7 @@ ptdr_status ptdr_decompose_host(const void* const* h_A, void* const* h_C, int co
                                 ptdr_dtype c_type, int n, ptdr_precision prec, void* d_scratch,
                                 size_t d_scratch_bytes, void* stream)
 {
+    PTDR_TRACE();
     if (!h_A || !h_C || count < 1) return PTDR_ERR_INVALID_ARG;
     for (int i = 0; i < count; ++i)
         if (!h_A[i] || !h_C[i]) return PTDR_ERR_INVALID_ARG;

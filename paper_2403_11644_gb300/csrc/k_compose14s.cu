@@ -44,7 +44,6 @@ constexpr int kRowStride = 65;             // pass 1 buffer: 128 zb x 64 zl, pad
 constexpr int kTileStride = 129;           // pass 2 buffer: 64 masks x 128 zl, padded (float2)
 constexpr int kSmemElems = kT * kRowStride; // 8320 float2 >= 64 x 129 and the 128 x 64 A tile
 constexpr int kSmemBytes = kSmemElems * 8 + 128;
-constexpr long long kSpinLimit = 1ll << 24;
 constexpr int kPerRound = 4 * kT;          // 256 half-row items + 256 half-tile items
 constexpr int kItems = (kTiles + 1) * kPerRound;
 constexpr int kDone = 2 * kT;              // items per x-tile and pass
@@ -70,12 +69,19 @@ __device__ __forceinline__ int ld_acquire(const int* p)
     return v;
 }
 
-// Bounded wait by one thread for *p >= target; records a timeout and gives up.
-__device__ __forceinline__ void wait_count(const int* p, int target, unsigned int* st)
+__device__ __forceinline__ unsigned long long now_ns()
 {
-    long long spins = 0;
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait by one thread for *p >= target; records a timeout and gives up.
+__device__ __forceinline__ void wait_count(const int* p, int target, unsigned long long limit_ns, unsigned int* st)
+{
+    const unsigned long long t0 = now_ns();
     while (ld_acquire(p) < target) {
-        if (++spins > kSpinLimit) {
+        if (now_ns() - t0 > limit_ns) {
             report_status(st, PTDR_ERR_TIMEOUT);
             return;
         }
@@ -90,6 +96,7 @@ struct ComposeTables {
     int* done1;    // half-row items finished per x-tile
     int* done2;    // half-tile items finished per x-tile
     float2* stage; // kSlots x 128 rows x 2^14
+    unsigned long long wait_ns; // bound of every wait for another CTA
 };
 
 __global__ void __launch_bounds__(kThreads, 2)
@@ -149,7 +156,7 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
             for (int i = 0; i < 32; ++i) buf[(32 * q + i) * kRowStride + zloc] = v[i];
             // the staging slot is free once x-tile xt - kSlots has been read from it
-            if (t == 0 && xt >= kSlots) wait_count(tab.done2 + (xt - kSlots), kDone, st);
+            if (t == 0 && xt >= kSlots) wait_count(tab.done2 + (xt - kSlots), kDone, tab.wait_ns, st);
             __syncthreads();
             // round b: zb bits 5-6, then contiguous staging stores S[xl][128 cb + zl]
             float2* srow = tab.stage + ((size_t)(xt % kSlots) * kT + xl) * kN + kH * h + zloc;
@@ -174,7 +181,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             const int jj = j - 2 * kT;
             const int xt = r - 1, cb = jj >> 1, h = jj & 1;
             if (xt < 0) { __syncthreads(); continue; }
-            if (t == 0) wait_count(tab.done1 + xt, kDone, st);
+            if (t == 0) wait_count(tab.done1 + xt, kDone, tab.wait_ns, st);
             __syncthreads();
             const int R = cb ^ xt;
             // staging rows xl = 64 h + xloc, columns 128 cb .. 128 cb + 127 -> buf[xloc][zl]
@@ -286,6 +293,7 @@ cudaError_t launch_compose14_staged(const void* C, void* A, double scale, void* 
     tab.done1 = (int*)(w + 64);
     tab.done2 = (int*)(w + 64 + 4 * kTiles);
     tab.stage = (float2*)(w + 4096);
+    tab.wait_ns = wait_limit_ns();
     if ((e = cudaMemsetAsync(ws, 0, 4096, s)) != cudaSuccess) return e;
     k_compose14_staged<<<grid, kThreads, kSmemBytes, s>>>((const float2*)C, (float2*)A, (float)scale, tab, st);
     return cudaGetLastError();

@@ -1,5 +1,9 @@
-// Dense n = 14 decomposition, complex64 -> complex64, FP32 arithmetic, as two
-// passes over an L2-resident staging buffer with contiguous HBM traffic.
+// Dense n = 14 and n = 15 decompositions, complex64 -> complex64, FP32
+// arithmetic, as two passes over an L2-resident staging buffer with
+// contiguous HBM traffic.  (Written out below for n = 14; at n = 15 the
+// transform across column blocks has 8 bits, as a 5-bit and a 3-bit register
+// round, row items cover 32 of a mask's 128 z_lo values, and two staging
+// slots of 32 MiB replace four of 16 MiB.)
 //
 // The XOR shear d_x[k] = A[k ^ x][k] maps 128 x 128 tiles onto 128 x 128
 // tiles: with x = 128 xt + xl and k = 128 cb + cl, the entries of masks
@@ -37,21 +41,31 @@ namespace ptdr {
 
 namespace {
 
-constexpr int kLog = 14;
-constexpr int kN = 1 << kLog;
 constexpr int kT = 128;                     // tile edge / masks per x-tile
-constexpr int kH = 64;                      // half tile: masks (pass 1) or z_lo values (pass 2) per item
-constexpr int kTiles = kN / kT;             // 128 x-tiles, 128 column blocks
+constexpr int kH = 64;                      // half tile: masks per tile item
 constexpr int kThreads = 256;
-constexpr int kSlots = 4;                   // staging slots (x-tiles in flight)
 constexpr int kYaStride = 129;              // pass 1 transpose: 64 rows x 128, padded (float2)
-constexpr int kYbStride = 65;               // pass 2 transpose: 128 rows x 64, padded (float2)
-constexpr int kSmemElems = kT * kYbStride;  // 8320 float2 >= 128 x 64 tile and 64 x 129
+constexpr int kSmemElems = 8448;            // float2: >= 64 x 129 and every row item's 2^RB x (ZL + 1)
 constexpr int kSmemBytes = kSmemElems * 8 + 128;
-constexpr long long kSpinLimit = 1ll << 24;
-constexpr int kPerRound = 4 * kT;           // 256 half-tile items + 256 half-row items
-constexpr int kItems = (kTiles + 1) * kPerRound;
-constexpr int kDone = 2 * kT;               // items per x-tile and pass
+
+// Sizes for n = LOG (14 or 15).  Row items cover ZL of the 128 z_lo values of
+// one mask over all 2^(LOG-7) column blocks (8192 values, 64 KiB, at both n);
+// the transform over the column-block bits runs as a 5-bit register round and
+// an RB-bit one.
+template <int LOG> struct Geo {
+    static constexpr int kN = 1 << LOG;
+    static constexpr int kTiles = kN / kT;          // x-tiles = column blocks
+    static constexpr int kCbBits = LOG - 7;         // transform bits across column blocks
+    static constexpr int kRb = kCbBits - 5;         // second-round bits (2 or 3)
+    static constexpr int kZl = 8192 >> kCbBits;     // z_lo values per row item (64 or 32)
+    static constexpr int kYb = kZl + 1;             // padded row-item transpose stride
+    static constexpr int kTileItems = 2 * kTiles;   // half tiles per x-tile
+    static constexpr int kRowItems = kT * (kT / kZl);
+    static constexpr int kPerRound = kTileItems + kRowItems;
+    static constexpr int kItems = (kTiles + 1) * kPerRound;
+    static constexpr int kSlots = LOG == 14 ? 4 : 2; // staging slots: 64 MiB of L2 either way
+    static_assert((1 << kCbBits) * kYb <= kSmemElems, "row item fits the shared buffer");
+};
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -76,12 +90,21 @@ __device__ __forceinline__ int ld_acquire(const int* p)
     return v;
 }
 
-// Bounded wait by thread 0 for *p >= target; records a timeout and gives up.
-__device__ __forceinline__ void wait_count(const int* p, int target, unsigned int* st)
+__device__ __forceinline__ unsigned long long now_ns()
 {
-    long long spins = 0;
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait by thread 0 for *p >= target; records a timeout and gives up
+// (the item then runs on whatever the slot holds: no hang, and the status word
+// reports the result as invalid).
+__device__ __forceinline__ void wait_count(const int* p, int target, unsigned long long limit_ns, unsigned int* st)
+{
+    const unsigned long long t0 = now_ns();
     while (ld_acquire(p) < target) {
-        if (++spins > kSpinLimit) {
+        if (now_ns() - t0 > limit_ns) {
             report_status(st, PTDR_ERR_TIMEOUT);
             return;
         }
@@ -96,11 +119,16 @@ struct StagedTables {
     int* done1; // tile items finished per x-tile
     int* done2; // row items finished per x-tile
     float2* stage; // kSlots x 128 rows x 2^14
+    unsigned long long wait_ns; // bound of every wait for another CTA
 };
 
+template <int LOG>
 __global__ void __launch_bounds__(kThreads, 2)
-    k_dense14_staged(const float2* __restrict__ A, float2* __restrict__ C, StagedTables tab, unsigned int* st)
+    k_dense_staged(const float2* __restrict__ A, float2* __restrict__ C, StagedTables tab, unsigned int* st)
 {
+    using G = Geo<LOG>;
+    constexpr int kN = G::kN, kTiles = G::kTiles, kPerRound = G::kPerRound, kItems = G::kItems,
+                  kSlots = G::kSlots, kZl = G::kZl, kYb = G::kYb, kRb = G::kRb;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ int s_item;
     const uint32_t raw_a = su32(smem_raw);
@@ -124,7 +152,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         if (item >= kItems) break;
         const int r = item / kPerRound, j = item % kPerRound;
 
-        if (j < 2 * kT) {
+        if (j < G::kTileItems) {
             // ------------------------------------------------ half-tile item
             // masks xl in [64 h, 64 h + 64) of x-tile xt, column block cb.
             // Row rl of the A tile contributes columns cl with cl bit 6 =
@@ -137,7 +165,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                 const int qc = t + kThreads * i; // 16-byte chunk: row qc >> 5, pair qc & 31
                 const int rl = qc >> 5;
                 const int b = ((rl >> 6) ^ h) & 1;
-                const uint64_t gi = ((uint64_t)(kT * R + rl) << kLog) + (uint64_t)(kT * cb + kH * b) + 2u * (qc & 31);
+                const uint64_t gi = ((uint64_t)(kT * R + rl) << LOG) + (uint64_t)(kT * cb + kH * b) + 2u * (qc & 31);
                 const float2* src = A + (in_bounds(st, gi + 1, (uint64_t)kN * kN) ? gi : 0);
                 asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(buf_a + (uint32_t)qc * 16u), "l"(src)
                              : "memory");
@@ -164,7 +192,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             for (int z = 0; z < 32; ++z) buf[xloc * kYaStride + 32 * g + z] = v[z];
             __syncthreads();
             // round b: cl bits 5-6; lane = z5, rows 8 w + i of the half tile
-            if (t == 0 && xt >= kSlots) wait_count(tab.done2 + (xt - kSlots), kDone, st);
+            if (t == 0 && xt >= kSlots) wait_count(tab.done2 + (xt - kSlots), G::kRowItems, tab.wait_ns, st);
             __syncthreads();
             float2* stage = tab.stage + ((size_t)(xt % kSlots) * kT + kH * h) * kN;
 #pragma unroll
@@ -184,48 +212,53 @@ __global__ void __launch_bounds__(kThreads, 2)
                 atomicAdd(tab.done1 + xt, 1);
             }
         } else {
-            // ------------------------------------------------ half-row item
-            // mask xl of x-tile xt, output columns z_lo in [64 h, 64 h + 64)
-            const int jj = j - 2 * kT;
-            const int xt = r - 1, xl = jj >> 1, h = jj & 1;
+            // ------------------------------------------------ row item
+            // mask xl of x-tile xt, output columns z_lo in [ZL h, ZL h + ZL) over all
+            // 2^(LOG-7) column blocks
+            const int jj = j - G::kTileItems;
+            const int xt = r - 1, xl = jj / (kT / kZl), h = jj % (kT / kZl);
             if (xt < 0) { __syncthreads(); continue; }
-            if (t == 0) wait_count(tab.done1 + xt, kDone, st);
+            if (t == 0) wait_count(tab.done1 + xt, G::kTileItems, tab.wait_ns, st);
             __syncthreads();
             const uint64_t x = (uint64_t)(kT * xt + xl);
-            const float2* srow = tab.stage + ((size_t)(xt % kSlots) * kT + xl) * kN + kH * h;
+            const float2* srow = tab.stage + ((size_t)(xt % kSlots) * kT + xl) * kN + kZl * h;
             // round a: cb bits 0-4; lanes take consecutive z_lo (coalesced L2 reads)
-            const int zloc = 32 * (warp & 1) + lane, q = warp >> 1;
+            const int zloc = t % kZl, q = t / kZl;
             float2 v[32];
 #pragma unroll
             for (int i = 0; i < 32; ++i) v[i] = __ldcg(srow + (size_t)(32 * q + i) * kT + zloc);
             wht_regs<5>(v);
 #pragma unroll
-            for (int i = 0; i < 32; ++i) buf[(32 * q + i) * kYbStride + zloc] = v[i];
+            for (int i = 0; i < 32; ++i) buf[(32 * q + i) * kYb + zloc] = v[i];
             __syncthreads();
-            // this item's half of the staging row is consumed: drop its lines from
-            // L2 without write-back (4 lines of 128 bytes per column block)
+            // this item's part of the staging row is consumed: drop its lines from
+            // L2 without write-back (kZl * 8 / 128 lines of 128 bytes per column block)
+            {
+                constexpr int kLinesPerCb = kZl / 16, kLines = kTiles * kLinesPerCb;
 #pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                const int ln = t + kThreads * i; // 512 lines
-                const float2* p = srow + (size_t)(ln >> 2) * kT + 16 * (ln & 3);
-                asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
+                for (int i = 0; i < kLines / kThreads; ++i) {
+                    const int ln = t + kThreads * i;
+                    const float2* p = srow + (size_t)(ln / kLinesPerCb) * kT + 16 * (ln % kLinesPerCb);
+                    asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
+                }
             }
-            // round b: cb bits 5-6, then phase, scale and contiguous stores
-            float2* out = C + (x << kLog) + kH * h;
+            // round b: cb bits 5 .. LOG-8, then phase, scale and contiguous stores
+            constexpr int kPb = kZl / 8; // (c5, z_lo) pairs per thread: 32 kZl / 256
+            float2* out = C + (x << LOG) + kZl * h;
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int c5 = 8 * q + i;
-                float2 e[4];
+            for (int i = 0; i < kPb; ++i) {
+                const int c5 = kPb * q + i;
+                float2 e[1 << kRb];
 #pragma unroll
-                for (int gg = 0; gg < 4; ++gg) e[gg] = buf[(32 * gg + c5) * kYbStride + zloc];
-                wht_regs<2>(e);
+                for (int gg = 0; gg < (1 << kRb); ++gg) e[gg] = buf[(32 * gg + c5) * kYb + zloc];
+                wht_regs<kRb>(e);
 #pragma unroll
-                for (int gg = 0; gg < 4; ++gg) {
+                for (int gg = 0; gg < (1 << kRb); ++gg) {
                     const uint64_t zoff = (uint64_t)(kT * (32 * gg + c5) + zloc);
-                    const uint64_t z = zoff + (uint64_t)(kH * h);
+                    const uint64_t z = zoff + (uint64_t)(kZl * h);
                     const float2 w = e[gg];
                     const float2 o = phase_neg_i(w, (int)(__popcll(x & z) & 3), scale);
-                    if (in_bounds(st, (x << kLog) + z, (uint64_t)kN * kN)) __stcs(out + zoff, o);
+                    if (in_bounds(st, (x << LOG) + z, (uint64_t)kN * kN)) __stcs(out + zoff, o);
                 }
             }
             __syncthreads();
@@ -239,17 +272,21 @@ __global__ void __launch_bounds__(kThreads, 2)
 
 // ------------------------------------------------------------------ host
 
-size_t dense14_staged_workspace()
+size_t dense_staged_workspace(int n)
 {
-    // counters (head, done1[128], done2[128]) padded to 4 KiB, then the slots
-    return 4096 + (size_t)kSlots * kT * kN * sizeof(float2);
+    // counters (head, done1[x-tiles], done2[x-tiles]) padded to 4 KiB, then the slots:
+    // 4 x 16 MiB at n = 14, 2 x 32 MiB at n = 15
+    return n == 14 ? 4096 + (size_t)Geo<14>::kSlots * kT * Geo<14>::kN * sizeof(float2)
+                   : 4096 + (size_t)Geo<15>::kSlots * kT * Geo<15>::kN * sizeof(float2);
 }
 
-cudaError_t launch_dense14_staged(const void* A, void* C, void* ws, unsigned int* st, cudaStream_t s)
+template <int LOG>
+static cudaError_t run_staged(const void* A, void* C, void* ws, unsigned int* st, cudaStream_t s)
 {
     static std::mutex mu;
     static int grid_for[128];
-    cudaError_t e = cudaFuncSetAttribute(k_dense14_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    auto kern = k_dense_staged<LOG>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
     if (e != cudaSuccess) return e;
     int dev = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
@@ -261,8 +298,7 @@ cudaError_t launch_dense14_staged(const void* A, void* C, void* ws, unsigned int
     if (grid == 0) {
         int sms = 0, per = 0;
         if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_dense14_staged, kThreads, kSmemBytes)) !=
-            cudaSuccess)
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kThreads, kSmemBytes)) != cudaSuccess)
             return e;
         grid = sms * (per > 0 ? per : 1);
         std::lock_guard<std::mutex> lk(mu);
@@ -272,11 +308,19 @@ cudaError_t launch_dense14_staged(const void* A, void* C, void* ws, unsigned int
     StagedTables tab;
     tab.head = (int*)w;
     tab.done1 = (int*)(w + 64);
-    tab.done2 = (int*)(w + 64 + 4 * kTiles);
+    tab.done2 = (int*)(w + 64 + 4 * Geo<LOG>::kTiles);
     tab.stage = (float2*)(w + 4096);
+    tab.wait_ns = wait_limit_ns();
     if ((e = cudaMemsetAsync(ws, 0, 4096, s)) != cudaSuccess) return e;
-    k_dense14_staged<<<grid, kThreads, kSmemBytes, s>>>((const float2*)A, (float2*)C, tab, st);
+    kern<<<grid, kThreads, kSmemBytes, s>>>((const float2*)A, (float2*)C, tab, st);
     return cudaGetLastError();
+}
+
+cudaError_t launch_dense_staged(int n, const void* A, void* C, void* ws, unsigned int* st, cudaStream_t s)
+{
+    if (n == 14) return run_staged<14>(A, C, ws, st, s);
+    if (n == 15) return run_staged<15>(A, C, ws, st, s);
+    return cudaErrorInvalidValue;
 }
 
 } // namespace ptdr

@@ -106,12 +106,21 @@ constexpr int kLag = 2;                                 // row jobs of x-tile r 
 constexpr int kPerRound = 2 * kT;
 constexpr int kItems = (kTiles + kLag) * kPerRound;
 constexpr int kDoneTarget = kT; // jobs per finished x-tile pass
-constexpr unsigned long long kWaitNs = 1000000000ull; // bound of every wait: 1 s
+// Bound of the final wait for this CTA's own tensor-map copies still in flight
+// after an abort (they land in microseconds; the CTA must not exit before).
+constexpr unsigned long long kDrainNs = 100000000ull; // 100 ms
 constexpr uint16_t kHPos = 0x3C00u, kHNeg = 0xBC00u;  // +2^-7, -2^-7 in bf16
 
 static_assert(kSlots >= kLag + 2, "a staging slot is rewritten only after its row jobs were dequeued");
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Per-CTA control block in shared memory: the abort flag every role polls and
+// the bound of every wait for another role or another CTA (a launch parameter).
+struct Ctl {
+    volatile int abort;
+    unsigned long long wait_ns;
+};
 
 __device__ __forceinline__ unsigned long long now_ns()
 {
@@ -128,11 +137,11 @@ __device__ __forceinline__ int ld_acquire(const int* p)
 }
 
 // Bounded wait for *p >= target (one thread).  False on time-out or abort.
-__device__ __forceinline__ bool wait_count(const int* p, int target, const volatile int* abort_flag)
+__device__ __forceinline__ bool wait_count(const int* p, int target, Ctl* ctl)
 {
     const unsigned long long t0 = now_ns();
     while (ld_acquire(p) < target) {
-        if (*abort_flag || now_ns() - t0 > kWaitNs) return false;
+        if (ctl->abort || now_ns() - t0 > ctl->wait_ns) return false;
         __nanosleep(128);
     }
     return true;
@@ -152,13 +161,13 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
 }
 
 // Bounded wait for the phase with the given parity to complete (one thread).
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const volatile int* abort_flag)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, Ctl* ctl)
 {
     if (mbar_try(bar, parity)) return true;
     const unsigned long long t0 = now_ns();
     for (;;) {
         if (mbar_try(bar, parity)) return true;
-        if (*abort_flag || now_ns() - t0 > kWaitNs) return false;
+        if (ctl->abort || now_ns() - t0 > ctl->wait_ns) return false;
     }
 }
 
@@ -199,13 +208,13 @@ __device__ __forceinline__ void lds128(uint32_t addr, float& a, float& b, float&
 }
 
 // Lane 0 of the warp runs a bounded mbarrier wait; every lane gets the result.
-__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, const volatile int* abort_flag, int lane,
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, Ctl* ctl, int lane,
                                           unsigned int* st)
 {
     int ok = 1;
-    if (lane == 0 && !mbar_wait(bar, parity, abort_flag)) {
+    if (lane == 0 && !mbar_wait(bar, parity, ctl)) {
         report_status(st, PTDR_ERR_TIMEOUT);
-        *const_cast<volatile int*>(abort_flag) = 1;
+        ctl->abort = 1;
         ok = 0;
     }
     return __shfl_sync(0xffffffffu, ok, 0) != 0;
@@ -303,6 +312,7 @@ struct TcPipeTables {
     int* done1;    // tile jobs finished per x-tile (x 8 epilogue warps)
     int* done2;    // row jobs finished per x-tile (x 8 epilogue warps)
     float2* stage; // kSlots x 128 rows x 2^14
+    unsigned long long wait_ns; // bound of every wait for another role or CTA
 };
 
 // kRealOut: C holds float32 real parts only (the Hermitian real-output mode:
@@ -316,7 +326,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     __shared__ __align__(8) unsigned long long raw_full[kRawSlots], raw_empty[kRawSlots], op_full[kOpSlots],
         op_empty[kOpSlots], t_full[2], t_empty[2], e_done[2], p_done[2], bar_exit;
     __shared__ int s_jobq[8], s_pubq[4];
-    __shared__ volatile int s_abort;
+    __shared__ Ctl s_ctl;
+    __shared__ int s_q_issued, s_q_seen; // raw chunks copied / observed landed (drain at exit)
     __shared__ uint32_t s_tmem;
 
     const uint32_t raw_a = su32(smem_raw);
@@ -353,7 +364,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bar_exit)));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        s_abort = 0;
+        s_ctl.abort = 0;
+        s_ctl.wait_ns = tab.wait_ns;
+        s_q_issued = 0;
+        s_q_seen = 0;
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -380,9 +394,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             int xt = 0, idx = 0;
             if (job < kItems && !decode(job, tile, xt, idx)) continue; // empty slot of the first or last rounds
             int ok = 1;
-            if (lane == 0 && job < kItems && !tile && !wait_count(tab.done1 + xt, kDoneTarget, &s_abort)) {
+            if (lane == 0 && job < kItems && !tile && !wait_count(tab.done1 + xt, kDoneTarget, &s_ctl)) {
                 report_status(st, PTDR_ERR_TIMEOUT);
-                s_abort = 1;
+                s_ctl.abort = 1;
                 ok = 0;
             }
             ok = __shfl_sync(0xffffffffu, ok, 0);
@@ -392,7 +406,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     s_jobq[J & 7] = -1;
                     const uint32_t sl = Q % kRawSlots;
                     if (Q < (uint32_t)kRawSlots ||
-                        mbar_wait(su32(&raw_empty[sl]), (Q / kRawSlots - 1) & 1, &s_abort))
+                        mbar_wait(su32(&raw_empty[sl]), (Q / kRawSlots - 1) & 1, &s_ctl))
                         mbar_arrive(su32(&raw_full[sl]));
                 }
                 break;
@@ -415,9 +429,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                 int go = 1;
                 if (lane == 0) {
                     if (Q >= (uint32_t)kRawSlots &&
-                        !mbar_wait(su32(&raw_empty[sl]), (Q / kRawSlots - 1) & 1, &s_abort)) {
+                        !mbar_wait(su32(&raw_empty[sl]), (Q / kRawSlots - 1) & 1, &s_ctl)) {
                         report_status(st, PTDR_ERR_TIMEOUT);
-                        s_abort = 1;
+                        s_ctl.abort = 1;
                         go = 0;
                     } else {
                         mbar_arrive_tx(su32(&raw_full[sl]), 32u * 1024u);
@@ -441,6 +455,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (quit) break;
             ++J;
         }
+        if (lane == 0) s_q_issued = (int)Q; // chunks whose copies were issued
     } else if (warp < kLoadWarps) {
         // ============================================================ loaders
         // Lane l takes K row l of each chunk (m = 32 c + l), which sits in row l of
@@ -465,7 +480,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             bool quit = false;
             for (int c = 0; c < kChunks; ++c, ++Q) {
                 const uint32_t rs = Q % kRawSlots, os = Q % kOpSlots;
-                if (!warp_wait(su32(&raw_full[rs]), (Q / kRawSlots) & 1, &s_abort, lane, st)) {
+                if (!warp_wait(su32(&raw_full[rs]), (Q / kRawSlots) & 1, &s_ctl, lane, st)) {
                     quit = true;
                     break;
                 }
@@ -516,7 +531,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (lane == 0) mbar_arrive(su32(&raw_empty[rs]));
                 // the operand slot was last read by the MMAs of chunk Q - 2
                 if (Q >= (uint32_t)kOpSlots &&
-                    !warp_wait(su32(&op_empty[os]), (Q / kOpSlots - 1) & 1, &s_abort, lane, st)) {
+                    !warp_wait(su32(&op_empty[os]), (Q / kOpSlots - 1) & 1, &s_ctl, lane, st)) {
                     quit = true;
                     break;
                 }
@@ -559,6 +574,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             if (quit) break;
         }
+        if (lane == 0) atomicMax(&s_q_seen, (int)Q); // chunks seen landed by this warp
     } else if (warp < kMmaWarp) {
         // ============================================================ epilogue
         // warp e = warp - 8 reads TMEM lanes 32 q .. 32 q + 31 (q = warp & 3, the
@@ -581,21 +597,21 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t b = J & 1;
             int job = -1;
             if (lane == 0) {
-                if (mbar_wait(su32(&t_full[b]), (J >> 1) & 1, &s_abort)) {
+                if (mbar_wait(su32(&t_full[b]), (J >> 1) & 1, &s_ctl)) {
                     job = s_jobq[J & 7];
                     bool tl = false;
                     int xt = 0, ix = 0;
                     // a tile job may overwrite its staging slot once the row jobs
                     // of the x-tile that used it before have read it
                     if (job >= 0 && decode(job, tl, xt, ix) && tl && xt >= kSlots &&
-                        !wait_count(tab.done2 + (xt - kSlots), kDoneTarget, &s_abort)) {
+                        !wait_count(tab.done2 + (xt - kSlots), kDoneTarget, &s_ctl)) {
                         report_status(st, PTDR_ERR_TIMEOUT);
-                        s_abort = 1;
+                        s_ctl.abort = 1;
                         job = -1;
                     }
                 } else {
                     report_status(st, PTDR_ERR_TIMEOUT);
-                    s_abort = 1;
+                    s_ctl.abort = 1;
                 }
             }
             job = __shfl_sync(0xffffffffu, job, 0);
@@ -604,9 +620,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             // this barrier pair first (so that no phase of it is skipped)
             auto hand_off = [&]() {
                 if (lane == 0) {
-                    if (J >= 2 && !mbar_wait(su32(&p_done[b]), ((J >> 1) - 1) & 1, &s_abort)) {
+                    if (J >= 2 && !mbar_wait(su32(&p_done[b]), ((J >> 1) - 1) & 1, &s_ctl)) {
                         report_status(st, PTDR_ERR_TIMEOUT);
-                        s_abort = 1;
+                        s_ctl.abort = 1;
                     }
                     mbar_arrive(su32(&e_done[b]));
                 }
@@ -721,7 +737,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint32_t os = Q % kOpSlots;
                 int go = 1, tl = 1;
                 if (lane == 0) {
-                    bool ok = mbar_wait(su32(&op_full[os]), (Q / kOpSlots) & 1, &s_abort);
+                    bool ok = mbar_wait(su32(&op_full[os]), (Q / kOpSlots) & 1, &s_ctl);
                     if (ok && c == 0) {
                         const int job = s_jobq[J & 7];
                         if (job < 0) {
@@ -729,12 +745,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                             mbar_arrive(su32(&t_full[b]));
                         } else {
                             tl = (job % kPerRound) < kT;
-                            if (J >= 2) ok = mbar_wait(su32(&t_empty[b]), ((J >> 1) - 1) & 1, &s_abort);
+                            if (J >= 2) ok = mbar_wait(su32(&t_empty[b]), ((J >> 1) - 1) & 1, &s_ctl);
                         }
                     }
                     if (!ok) {
                         report_status(st, PTDR_ERR_TIMEOUT);
-                        s_abort = 1;
+                        s_ctl.abort = 1;
                         go = 0;
                     }
                 }
@@ -789,7 +805,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                              su32(&bar_exit))
                          : "memory");
             const unsigned long long t0 = now_ns();
-            while (!mbar_try(su32(&bar_exit), 0) && now_ns() - t0 < kWaitNs) {
+            while (!mbar_try(su32(&bar_exit), 0) && now_ns() - t0 < kDrainNs) {
             }
         }
         __syncwarp();
@@ -802,11 +818,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t b = J & 1;
             int job = -1;
             if (lane == 0) {
-                if (mbar_wait(su32(&e_done[b]), (J >> 1) & 1, &s_abort)) {
+                if (mbar_wait(su32(&e_done[b]), (J >> 1) & 1, &s_ctl)) {
                     job = s_pubq[J & 3];
                 } else {
                     report_status(st, PTDR_ERR_TIMEOUT);
-                    s_abort = 1;
+                    s_ctl.abort = 1;
                 }
                 bool tl = false;
                 int xt = 0, ix = 0;
@@ -823,6 +839,20 @@ __global__ void __launch_bounds__(kThreads, 1)
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == kMmaWarp) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+    // After an abort the loaders may have left chunks whose tensor-map copies are
+    // still landing in this CTA's shared memory: wait (bounded) for each of them
+    // before the CTA exits.  Each such chunk is the last fill of its ring slot (a
+    // slot is refilled only after the loaders release it), so its phase parity
+    // identifies it.  Without an abort every chunk was seen landed: no wait.
+    if (t == 0) {
+        const int q0 = max(s_q_seen, s_q_issued - kRawSlots);
+        for (int q = q0; q < s_q_issued; ++q) {
+            const uint32_t bar = su32(&raw_full[q % kRawSlots]), par = (uint32_t)(q / kRawSlots) & 1u;
+            const unsigned long long t0 = now_ns();
+            while (!mbar_try(bar, par) && now_ns() - t0 < kDrainNs) {
+            }
+        }
+    }
 }
 
 // ------------------------------------------------------------------ host
@@ -894,6 +924,7 @@ cudaError_t launch_tc14_pipe(const void* A, void* C, bool real_out, void* ws, un
     tab.done1 = (int*)(w + 64);
     tab.done2 = (int*)(w + 64 + 4 * kTiles);
     tab.stage = (float2*)(w + 4096);
+    tab.wait_ns = wait_limit_ns();
     CUtensorMap tmA, tmS;
     if (!encode_boxes(&tmA, A, kN, 2 * kN) || !encode_boxes(&tmS, tab.stage, (uint64_t)kSlots * kT * kT, 2 * kT))
         return cudaErrorInvalidValue;

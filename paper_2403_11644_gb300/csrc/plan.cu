@@ -14,11 +14,16 @@ static int ilog2(size_t v)
 
 std::vector<StridedPass> strided_schedule(int b0, int n, size_t elem_bytes)
 {
+    return strided_schedule_budget(b0, n, elem_bytes, kTileBytes);
+}
+
+std::vector<StridedPass> strided_schedule_budget(int b0, int n, size_t elem_bytes, size_t tile_bytes)
+{
     // Each strided tile is 2^nb rows (the bits transformed) x 2^log_w
     // consecutive elements (>= 32 bytes so that every row piece is a whole
     // sector); as many bits per pass as the tile budget allows.
     std::vector<StridedPass> out;
-    const int tile_log = ilog2(kTileBytes / elem_bytes);
+    const int tile_log = ilog2(tile_bytes / elem_bytes);
     const int min_w = std::max(0, ilog2(32 / elem_bytes));
     int b = b0;
     while (b < n) {
@@ -102,7 +107,7 @@ ptdr_status make_dense_plan(bool compose, int n, ptdr_dtype in_t, ptdr_dtype out
         p.kernel = DenseKernel::Row14;
         p.single = true;
         // the clustered complex64 kernel exchanges through a scratch in the workspace
-        if (in_t == PTDR_C64 && out_t == PTDR_C64) p.ws_bytes = dense14_staged_workspace();
+        if (in_t == PTDR_C64 && out_t == PTDR_C64) p.ws_bytes = dense_staged_workspace(14);
         *plan = p;
         return PTDR_OK;
     }
@@ -144,9 +149,44 @@ ptdr_status make_dense_plan(bool compose, int n, ptdr_dtype in_t, ptdr_dtype out
             p.log_r = 0;
             p.passes = strided_schedule(p.log_l, n, S);
         }
+        // n = 15 FP32 complex64 -> complex64: the staged two-pass kernel (the
+        // multi-pass fields above stay the plan for unaligned buffers)
+        if (!compose && n == 15 && p.calc == Calc::F32 && in_t == PTDR_C64 && out_t == PTDR_C64) {
+            p.kernel = DenseKernel::Staged15;
+            p.ws_bytes = std::max(p.ws_bytes, dense_staged_workspace(15));
+        }
     }
     *plan = p;
     return PTDR_OK;
+}
+
+bool multipass_tunable(const DensePlan& p)
+{
+    // (the staged n = 14/15 kernels and the fixed-point path have their own schedules)
+    return !p.single && p.kernel == DenseKernel::Tiles;
+}
+
+bool apply_multipass_tuning(DensePlan* p, const TuneParams& t)
+{
+    if (!multipass_tunable(*p)) return false;
+    if (t.tile_log2 < 13 || t.tile_log2 > 17 || t.pass_tile_log2 < 13 || t.pass_tile_log2 > 17 ||
+        t.masks_log2 < 0 || t.masks_log2 > 4 || (t.threads != 256 && t.threads != 512))
+        return false;
+    const size_t S = p->calc == Calc::F64 ? 16 : 8;
+    const int elems_log = t.tile_log2 - ilog2(S);
+    int log_r = p->compose ? 0 : t.masks_log2;
+    while (log_r > 0 && p->chunk % ((size_t)1 << log_r)) --log_r; // a chunk holds whole tiles of masks
+    const int log_l = elems_log - log_r;
+    if (log_l < 5 || log_l >= p->n) return false; // the first pass must leave bits for the strided passes
+    DensePlan q = *p;
+    q.kernel = DenseKernel::Tiles;
+    q.log_r = log_r;
+    q.log_l = log_l;
+    q.threads = t.threads;
+    q.pass_threads = t.threads;
+    q.passes = strided_schedule_budget(log_l, p->n, S, (size_t)1 << t.pass_tile_log2);
+    *p = q;
+    return true;
 }
 
 ptdr_status execute_dense(const DensePlan& p, const void* in, void* out, void* ws, double scale,
@@ -188,11 +228,20 @@ ptdr_status execute_dense(const DensePlan& p, const void* in, void* out, void* w
         g.kernel = DenseKernel::Tiles;
         return execute_dense(g, in, out, ws, scale, st, s);
     }
+    if (p.kernel == DenseKernel::Staged15) {
+        if (ws && (uintptr_t)in % 16 == 0 && (uintptr_t)out % 16 == 0) {
+            e = launch_dense_staged(15, in, out, ws, st, s);
+            return e == cudaSuccess ? PTDR_OK : PTDR_ERR_CUDA;
+        }
+        DensePlan g = p;
+        g.kernel = DenseKernel::Tiles;
+        return execute_dense(g, in, out, ws, scale, st, s);
+    }
     if (p.kernel == DenseKernel::Row14) {
         // complex64 -> complex64 with a 16-byte aligned input takes the
         // clustered tile kernel; other type pairs the one-mask-per-CTA kernel
         if (ws && p.in_t == PTDR_C64 && p.out_t == PTDR_C64 && (uintptr_t)in % 16 == 0 && (uintptr_t)out % 16 == 0)
-            e = launch_dense14_staged(in, out, ws, st, s);
+            e = launch_dense_staged(14, in, out, ws, st, s);
         else
             e = launch_row14(in, p.in_t, out, p.out_t, st, s);
         return e == cudaSuccess ? PTDR_OK : PTDR_ERR_CUDA;
@@ -260,7 +309,7 @@ ptdr_status execute_dense(const DensePlan& p, const void* in, void* out, void* w
             q.src_row0 = buf_row0;
             q.src_elems = buf_elems;
             q.dst_elems = last ? N * N : buf_elems;
-            q.threads = 512;
+            q.threads = p.pass_threads;
             if (!last) {
                 q.dst = buf;
                 q.store = Store::RowBuf;

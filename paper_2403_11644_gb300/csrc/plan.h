@@ -26,6 +26,8 @@ enum class DenseKernel {
     Tiles,      // generic tile kernels (any n, FP32/FP64)
     Row14,      // n = 14 FP32 decompose: staged two-pass kernel (complex64, 16-byte
                 // aligned), otherwise one CTA per mask with register rounds 5/5/4
+    Staged15,   // n = 15 FP32 decompose complex64 -> complex64 (16-byte aligned):
+                // staged two-pass kernel; otherwise the generic multi-pass plan
     Tc14,       // n = 14 split-bf16 decompose, tensor-core stage over column blocks
     Compose14,  // n = 14 FP32 compose complex64 -> complex64: staged two-pass kernel
     Rr,         // n = 9 .. 12 FP32 decompose complex64 -> complex64 (16-byte aligned):
@@ -46,8 +48,23 @@ struct DensePlan {
     std::vector<StridedPass> passes;
     bool buf_is_out = false; // intermediate lives in the output array
     uint64_t chunk = 0;      // masks per launch chunk (multi-pass)
+    int pass_threads = 512;  // threads per CTA of the strided passes
     size_t ws_bytes = 0;
 };
+
+// Parameters of a generic multi-pass plan chosen by the autotuner (tune.cu):
+// first-pass tile bytes and masks per tile, strided-pass tile bytes, threads.
+struct TuneParams {
+    int tile_log2, masks_log2, pass_tile_log2, threads;
+};
+// Whether the plan runs (or falls back to) the generic multi-pass kernels.
+bool multipass_tunable(const DensePlan& p);
+// Rebuilds the first-pass tile and the strided passes of a multi-pass plan
+// with the given parameters (workspace and chunking unchanged); false if the
+// plan is not multi-pass or the parameters do not fit it.
+bool apply_multipass_tuning(DensePlan* p, const TuneParams& t);
+// The tuned parameters cached for this plan on device `dev`, if any.
+bool tuned_params_for(int dev, const DensePlan& p, TuneParams* out);
 
 ptdr_status make_dense_plan(bool compose, int n, ptdr_dtype in_t, ptdr_dtype out_t,
                             ptdr_precision prec, DensePlan* plan);
@@ -56,11 +73,13 @@ ptdr_status execute_dense(const DensePlan& plan, const void* in, void* out, void
 
 // Splits bits [b0, n) into strided passes whose tiles fit kTileBytes.
 std::vector<StridedPass> strided_schedule(int b0, int n, size_t elem_bytes);
+// The same with a tile budget of tile_bytes instead of kTileBytes.
+std::vector<StridedPass> strided_schedule_budget(int b0, int n, size_t elem_bytes, size_t tile_bytes);
 
 cudaError_t launch_row14(const void* A, ptdr_dtype a_t, void* C, ptdr_dtype c_t,
                          unsigned int* status, cudaStream_t s);
-cudaError_t launch_dense14_staged(const void* A, void* C, void* ws, unsigned int* status, cudaStream_t s);
-size_t dense14_staged_workspace();
+cudaError_t launch_dense_staged(int n, const void* A, void* C, void* ws, unsigned int* status, cudaStream_t s);
+size_t dense_staged_workspace(int n);
 cudaError_t launch_tc14_pipe(const void* A, void* C, bool real_out, void* ws, unsigned int* status, cudaStream_t s);
 size_t tc14_pipe_workspace();
 cudaError_t launch_compose14_staged(const void* C, void* A, double scale, void* ws, unsigned int* status,
@@ -77,5 +96,8 @@ ptdr_status status_word(int dev, unsigned int** out);
 ptdr_status check_device_ptr(const void* p);
 bool overlaps(const void* a, size_t na, const void* b, size_t nb);
 bool fault_injected(const char* what);
+// Bound (ns) of the device-side waits of the persistent kernels for other CTAs:
+// PTDR_WAIT_NS from the environment at each launch, default 1 s, at most 60 s.
+unsigned long long wait_limit_ns();
 
 } // namespace ptdr

@@ -75,6 +75,16 @@ bool fault_injected(const char* what)
     return f && std::strcmp(f, what) == 0;
 }
 
+unsigned long long wait_limit_ns()
+{
+    const char* v = std::getenv("PTDR_WAIT_NS");
+    if (!v || !*v) return 1000000000ull;
+    char* end = nullptr;
+    const unsigned long long ns = std::strtoull(v, &end, 10);
+    if (end == v || ns == 0) return 1000000000ull;
+    return std::min<unsigned long long>(ns, 60000000000ull);
+}
+
 } // namespace ptdr
 
 using namespace ptdr;
@@ -126,6 +136,8 @@ ptdr_status run_dense(bool compose, const void* in, ptdr_dtype in_t, void* out, 
     v = status_word(dev, &st);
     if (v != PTDR_OK) return v;
     if (fault_injected("launch")) return PTDR_ERR_CUDA;
+    TuneParams tp;
+    if (tuned_params_for(dev, plan, &tp)) apply_multipass_tuning(&plan, tp); // schedule from the autotuner's cache
     return execute_dense(plan, in, out, ws, scale, st, (cudaStream_t)stream);
 }
 
@@ -137,6 +149,7 @@ ptdr_status ptdr_decompose(const void* A, ptdr_dtype a_type, void* C, ptdr_dtype
                            ptdr_precision prec, void* workspace, size_t workspace_bytes,
                            void* stream)
 {
+    PTDR_TRACE();
     return run_dense(false, A, a_type, C, c_type, n, std::ldexp(1.0, -n), prec, workspace,
                      workspace_bytes, stream);
 }
@@ -145,9 +158,81 @@ ptdr_status ptdr_compose(const void* C, ptdr_dtype c_type, void* A, ptdr_dtype a
                          double scale, ptdr_precision prec, void* workspace,
                          size_t workspace_bytes, void* stream)
 {
+    PTDR_TRACE();
     if (!std::isfinite(scale)) return PTDR_ERR_INVALID_ARG;
     return run_dense(true, C, c_type, A, a_type, n, scale, prec, workspace, workspace_bytes,
                      stream);
+}
+
+ptdr_status ptdr_autotune(ptdr_op op, int n, ptdr_dtype in_type, ptdr_dtype out_type, ptdr_precision prec,
+                          const void* in, void* out, void* workspace, size_t workspace_bytes, void* stream,
+                          ptdr_tune_params* best)
+{
+    PTDR_TRACE();
+    if (!best || (op != PTDR_OP_DECOMPOSE && op != PTDR_OP_COMPOSE)) return PTDR_ERR_INVALID_ARG;
+    const bool compose = op == PTDR_OP_COMPOSE;
+    ptdr_status v = validate_dense(in, in_type, out, out_type, n, prec, compose);
+    if (v != PTDR_OK) return v;
+    DensePlan plan;
+    v = make_dense_plan(compose, n, in_type, out_type, prec, &plan);
+    if (v != PTDR_OK) return v;
+    if (plan.ws_bytes > 0 && (!workspace || workspace_bytes < plan.ws_bytes)) return PTDR_ERR_WORKSPACE;
+    if (!multipass_tunable(plan)) return PTDR_ERR_UNSUPPORTED; // no strided passes to schedule
+    int dev = 0;
+    v = device_ready(&dev);
+    if (v != PTDR_OK) return v;
+    if (check_device_ptr(in) != PTDR_OK || check_device_ptr(out) != PTDR_OK ||
+        (plan.ws_bytes > 0 && check_device_ptr(workspace) != PTDR_OK))
+        return PTDR_ERR_INVALID_ARG;
+    unsigned int* st = nullptr;
+    v = status_word(dev, &st);
+    if (v != PTDR_OK) return v;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return PTDR_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    const double scale = compose ? 1.0 : std::ldexp(1.0, -n);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return PTDR_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return PTDR_ERR_CUDA;
+    }
+    ptdr_status result = PTDR_ERR_UNSUPPORTED;
+    double best_ms = 1e300;
+    TuneParams best_p{};
+    for (int tl = 15; tl <= 17; ++tl)
+        for (int ml = 0; ml <= (compose ? 0 : 3); ++ml)
+            for (int pl = 15; pl <= 17; ++pl)
+                for (int th = 256; th <= 512; th *= 2) {
+                    DensePlan q = plan;
+                    const TuneParams t{tl, ml, pl, th};
+                    if (!apply_multipass_tuning(&q, t)) continue;
+                    // one warm-up launch, then the mean of two timed ones
+                    if (execute_dense(q, in, out, workspace, scale, st, s) != PTDR_OK) continue;
+                    cudaEventRecord(e0, s);
+                    bool ok = true;
+                    for (int r = 0; r < 2 && ok; ++r) ok = execute_dense(q, in, out, workspace, scale, st, s) == PTDR_OK;
+                    cudaEventRecord(e1, s);
+                    float ms = 0.f;
+                    if (!ok || cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                        cudaGetLastError();
+                        continue;
+                    }
+                    if (ms / 2 < best_ms) {
+                        best_ms = ms / 2;
+                        best_p = t;
+                        result = PTDR_OK;
+                    }
+                }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (result != PTDR_OK) return PTDR_ERR_CUDA;
+    best->tile_log2 = best_p.tile_log2;
+    best->masks_log2 = best_p.masks_log2;
+    best->pass_tile_log2 = best_p.pass_tile_log2;
+    best->threads = best_p.threads;
+    best->ms = best_ms;
+    return ptdr_tune_store(prop.name, op, n, in_type, out_type, prec, best);
 }
 
 ptdr_status ptdr_workspace_size(ptdr_op op, int n, ptdr_dtype a_type, ptdr_dtype c_type,

@@ -2,12 +2,24 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stddef.h>
 #include <stdint.h>
 
 #include "../../include/ptdr.h"
 
 namespace ptdr {
+
+// An NVTX range named after the entry point around each compute call of the C
+// ABI: profilers (Nsight Systems, ncu --nvtx) attribute the kernels to the
+// call; without an attached tool the push/pop cost a few nanoseconds.
+struct TraceRange {
+    explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange&) = delete;
+    TraceRange& operator=(const TraceRange&) = delete;
+};
+#define PTDR_TRACE() ::ptdr::TraceRange ptdr_trace_range_(__func__)
 
 // Which numeric path a launch takes.
 enum class Calc { F32, F64 };

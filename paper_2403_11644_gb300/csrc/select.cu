@@ -397,6 +397,7 @@ ptdr_status ptdr_coeff_select(int n, const void* C, ptdr_dtype c_type, double th
                               uint64_t* d_idx, void* d_val, size_t cap, unsigned long long* d_count, double* d_l1,
                               void* workspace, size_t workspace_bytes, void* stream)
 {
+    PTDR_TRACE();
     if (n < 1 || n > kMaxDenseN || !C || !valid_dtype(c_type) || !d_count || !d_l1) return PTDR_ERR_INVALID_ARG;
     if (!(threshold >= 0.0) || !std::isfinite(threshold)) return PTDR_ERR_INVALID_ARG;
     if (cap > 0 && (!d_idx || !d_val)) return PTDR_ERR_INVALID_ARG;

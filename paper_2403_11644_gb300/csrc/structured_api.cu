@@ -338,6 +338,7 @@ ptdr_status ptdr_decompose_structured(const void* bands, ptdr_dtype b_type, int 
                                       ptdr_dtype c_type, ptdr_precision prec, void* workspace,
                                       size_t workspace_bytes, void* stream)
 {
+    PTDR_TRACE();
     return decompose_band(bands, b_type, n, s, h_masks, n_masks, C, c_type, prec, workspace, workspace_bytes,
                           stream, nullptr);
 }
@@ -381,6 +382,7 @@ ptdr_status ptdr_decompose_antistructured(const void* antibands, ptdr_dtype b_ty
                                           const uint64_t* h_masks, size_t n_masks, void* C, ptdr_dtype c_type,
                                           ptdr_precision prec, void* workspace, size_t workspace_bytes, void* stream)
 {
+    PTDR_TRACE();
     std::vector<uint64_t> xb;
     ptdr_status v = band_masks_of(n, h_masks, n_masks, &xb);
     if (v != PTDR_OK) return v;

@@ -104,6 +104,31 @@ def compose(C: torch.Tensor, scale: float = 1.0, precision: str = "fp32", out_dt
     return A
 
 
+class TuneParams(ctypes.Structure):
+    """ptdr_tune_params: the schedule of a multi-pass plan chosen by the autotuner."""
+    _fields_ = [("tile_log2", ctypes.c_int), ("masks_log2", ctypes.c_int), ("pass_tile_log2", ctypes.c_int),
+                ("threads", ctypes.c_int), ("ms", ctypes.c_double)]
+
+
+def autotune(op: str, inp: torch.Tensor, out: torch.Tensor, precision: str, workspace=None) -> dict:
+    """Times the candidate schedules of the strided HBM passes of decompose/compose on these
+    buffers (out is overwritten) and caches the fastest for this GPU (and in the JSON file
+    PTDR_TUNE_CACHE names).  Returns the chosen schedule and its time."""
+    inp, out = _cuda(inp, "inp"), _cuda(out, "out")
+    n = _n_of(inp.shape[0])
+    code = _lib.OP_DECOMPOSE if op == "decompose" else _lib.OP_COMPOSE
+    a_dt, c_dt = (inp.dtype, out.dtype) if op == "decompose" else (out.dtype, inp.dtype)
+    wsb = workspace_size(op, n, a_dt, c_dt, precision)
+    ws = workspace if workspace is not None else (_workspace(wsb, inp.device) if wsb else None)
+    p = TuneParams()
+    check(_lib.load().ptdr_autotune(
+        code, n, _dtype_code(inp.dtype), _dtype_code(out.dtype), _prec(precision), ctypes.c_void_p(inp.data_ptr()),
+        ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(ws.data_ptr() if ws is not None else 0), wsb,
+        _stream(inp.device), ctypes.byref(p)), "ptdr_autotune")
+    return {"tile_log2": p.tile_log2, "masks_log2": p.masks_log2, "pass_tile_log2": p.pass_tile_log2,
+            "threads": p.threads, "ms": p.ms}
+
+
 def host_scratch_size(n: int, a_dtype, c_dtype, precision: str) -> int:
     """Device scratch bytes that decompose_host needs (two A, two C buffers, workspace)."""
     out = ctypes.c_size_t(0)

@@ -131,6 +131,20 @@ def test_n15_fp32_multipass():
     assert ptdr.last_device_status() == 0
 
 
+def test_n15_fp32_generic_multipass_for_unaligned_output():
+    """An output that is not 16-byte aligned takes the generic multi-pass plan (first
+    pass and strided HBM passes) instead of the staged kernel: sampled rows."""
+    A = workloads.dense_c64_direct(15, 152)
+    Ad = dev(A)
+    buf = torch.empty((1 << 30) + 1, dtype=torch.complex64, device="cuda")
+    C = buf[1:].view(1 << 15, 1 << 15)  # 8-byte aligned only
+    ptdr.decompose(Ad, precision="fp32", out=C)
+    xs = workloads.sample_masks(15, 152, count=6)
+    got = host(C[torch.from_numpy(xs.astype(np.int64)).cuda()])
+    assert rel_err(got, oracle.fwht(A, xs=xs)) <= TOL["fp32"]
+    assert ptdr.last_device_status() == 0
+
+
 def test_compose_n15_against_oracle():
     """n = 15 compose (multi-pass), complex64 coefficients fed to both sides, against the
     oracle's inverse FWHT: every XOR-diagonal of the result, mask chunk by mask chunk."""
@@ -293,8 +307,10 @@ def test_checked_build_small():
     for n in (3, 8, 15):
         A = dev(workloads.dense(n, 5, dtype=np.complex64) if n < 15 else workloads.dense_c64_direct(15, 5))
         C = torch.empty_like(A)
+        wsb = ptdr.workspace_size("decompose", n, A.dtype, C.dtype, "fp32")
+        ws = torch.empty(max(wsb, 1), dtype=torch.uint8, device="cuda")
         st = L.ptdr_decompose(ctypes.c_void_p(A.data_ptr()), _lib.C64, ctypes.c_void_p(C.data_ptr()),
-                              _lib.C64, n, _lib.PREC_FP32, None, 0,
+                              _lib.C64, n, _lib.PREC_FP32, ctypes.c_void_p(ws.data_ptr()), wsb,
                               ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
         assert st == 0
         assert L.ptdr_last_device_status(ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)) == 0

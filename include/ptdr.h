@@ -218,6 +218,39 @@ ptdr_status ptdr_antistructured_workspace_size(int n, int s, const uint64_t* h_m
                                                ptdr_precision prec, size_t* bytes);
 
 /*
+ * Matrix-free input (Sec. V.B: the decomposition does not need the input
+ * stored when its entries can be computed, e.g. from a function).
+ *
+ * The masks are processed in x-blocks of 2^a, a = min(7, n).  Block xt
+ * (masks xt 2^a .. xt 2^a + 2^a - 1) reads exactly the sheared tile set
+ *     S[i * 2^n + k] = A[(((k >> a) ^ xt) << a) + i][k],   i < 2^a, k < 2^n,
+ * (the 2^a x 2^a tiles (cb ^ xt, cb) of A, one per column block cb), and every
+ * tile of A belongs to exactly one block.  Before each block the library calls
+ * fill(user, n, xt, a, d_S, stream), which must enqueue on `stream` (or
+ * finish before returning) the writes of S into the device buffer d_S
+ * (2^a x 2^n elements of a_type, row-major) and return 0; a nonzero return
+ * stops the call with PTDR_ERR_INTERNAL.  The device then holds 2^a rows of A
+ * at a time instead of 2^n, and each entry is produced once.  fill runs on the
+ * calling thread, blocks in ascending xt.
+ */
+typedef int (*ptdr_tile_fn)(void* user, int n, uint64_t x_tile, int a, void* d_S, void* stream);
+
+/*
+ * ptdr_decompose_matrix_free -- ptdr_decompose with A produced block by block
+ * by `fill` (above).  n, a_type, C, c_type as for ptdr_decompose; prec FP64 or
+ * FP32 (generic tile kernels); workspace (256-byte aligned) of at least
+ * ptdr_matrix_free_workspace_size() bytes holds S and, for rows longer than
+ * one tile, the block's intermediate rows.
+ */
+ptdr_status ptdr_decompose_matrix_free(int n, ptdr_dtype a_type, ptdr_tile_fn fill, void* user, void* C,
+                                       ptdr_dtype c_type, ptdr_precision prec, void* workspace,
+                                       size_t workspace_bytes, void* stream);
+
+/* Workspace bytes for ptdr_decompose_matrix_free.  Host only. */
+ptdr_status ptdr_matrix_free_workspace_size(int n, ptdr_dtype a_type, ptdr_dtype c_type,
+                                            ptdr_precision prec, size_t* bytes);
+
+/*
  * ptdr_decompose_batched -- decomposes `count` independent matrices of
  * possibly different sizes in one persistent launch (the paper's forest of
  * independent subtrees, Sec. V.B, taken across matrices).

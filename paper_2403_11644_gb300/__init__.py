@@ -17,6 +17,7 @@ from .ptdr import (  # noqa: F401
     decompose_autograd,
     decompose_batched,
     decompose_host,
+    decompose_matrix_free,
     decompose_structured,
     hermitian_augment,
     host_scratch_size,

@@ -18,6 +18,10 @@ C64, C128, F32, F64 = 0, 1, 2, 3
 PREC_FP64, PREC_FP32, PREC_SPLIT_BF16_TC, PREC_FIXED_I128 = 0, 1, 2, 3
 OP_DECOMPOSE, OP_COMPOSE = 0, 1
 
+# fill(user, n, x_tile, a, d_S, stream) -> int: the matrix-free input's tile callback
+TILE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
+                           ctypes.c_void_p, ctypes.c_void_p)
+
 _lock = threading.Lock()
 _libs = {}
 
@@ -54,6 +58,8 @@ SIGNATURES = {
     "ptdr_coeff_hermitian_augment": [_i, _vp, _i, _vp, _i, _vp],
     "ptdr_coeff_select": [_i, _vp, _i, _d, ctypes.c_ulonglong, _vp, _vp, _sz, _vp, _vp, _vp, _sz, _vp],
     "ptdr_select_workspace_size": [_szp],
+    "ptdr_decompose_matrix_free": [_i, _i, _vp, _vp, _vp, _i, _i, _vp, _sz, _vp],
+    "ptdr_matrix_free_workspace_size": [_i, _i, _i, _i, _szp],
     "ptdr_autotune": [_i, _i, _i, _i, _i, _vp, _vp, _vp, _sz, _vp, _vp],
     "ptdr_tune_lookup": [ctypes.c_char_p, _i, _i, _i, _i, _i, _vp],
     "ptdr_tune_store": [ctypes.c_char_p, _i, _i, _i, _i, _i, _vp],

@@ -28,7 +28,8 @@ __global__ void __launch_bounds__(512) k_tile(TileLaunch p, unsigned int* st)
     const T scale = (T)p.scale;
 
     if (LD == Load::GatherA)
-        load_gather<T>(s, sm, (const InT*)p.src, p.n, x0, p.log_r, k0, p.log_l, p.src_elems, st);
+        load_gather<T>(s, sm, (const InT*)p.src, p.n, x0, p.log_r, k0, p.log_l, p.src_elems, st,
+                       p.src_row_mask ? p.src_row_mask : ~0ull);
     else if (LD == Load::RowPhaseC)
         load_row_phase<T>(s, sm, (const InT*)p.src, p.n, x0, p.log_r, k0, p.log_l, p.src_row0,
                           scale, p.src_elems, st);

@@ -71,6 +71,7 @@ struct TileLaunch {
     uint64_t src_elems, dst_elems; // extents for the checked build's index checks
     double scale;
     int threads;
+    uint64_t src_row_mask; // gather from rows r & mask of a sheared tile set (0: all of A)
 };
 
 // Strided pass over bits [b0, b1) of each row of an intermediate buffer,

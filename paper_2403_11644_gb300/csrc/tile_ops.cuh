@@ -100,12 +100,15 @@ __device__ void wht_bits(T2* s, const Smem& sm, int log_e, int b0, int b1)
 constexpr int kLoadBatch = 8;
 
 // d_x[k] = A[k ^ x][k] for the tile's masks x in [x0, x0 + 2^log_r) and
-// k in [k0, k0 + 2^log_l) (log_r <= log_l, both aligned).  Walked in the row
+// k in [k0, k0 + 2^log_l) (log_r <= log_l, both aligned).  With a row_mask the
+// source holds only the rows r & row_mask of a sheared tile set (the
+// matrix-free input): S[i][k] = A[((k >> a) ^ xt) 2^a + i][k].  Walked in the row
 // view: row r of A supplies the aligned block of 2^log_r columns r ^ x, so
 // consecutive threads read consecutive addresses.  Tile row = mask.
 template <typename T, typename InT>
 __device__ void load_gather(cplx_t<T>* s, const Smem& sm, const InT* A, int n, uint64_t x0,
-                            int log_r, uint64_t k0, int log_l, uint64_t lim, unsigned int* st)
+                            int log_r, uint64_t k0, int log_l, uint64_t lim, unsigned int* st,
+                            uint64_t row_mask = ~0ull)
 {
     const uint64_t N = 1ull << n;
     const uint64_t R = 1ull << log_r, L = 1ull << log_l;
@@ -119,7 +122,7 @@ __device__ void load_gather(cplx_t<T>* s, const Smem& sm, const InT* A, int n, u
             const uint64_t c = ((r ^ x0) & ~(R - 1)) + ((uint64_t)e & (R - 1));
             const int xl = (int)((r ^ c) - x0);
             const int kl = (int)(c - k0);
-            const uint64_t gi = r * N + c;
+            const uint64_t gi = (r & row_mask) * N + c;
             cplx_t<T>* d = s + sm.idx((xl << log_l) + kl);
             if (in_bounds(st, gi, lim)) {
                 const uint32_t da = (uint32_t)__cvta_generic_to_shared(d);
@@ -147,7 +150,7 @@ __device__ void load_gather(cplx_t<T>* s, const Smem& sm, const InT* A, int n, u
                 const uint64_t c = ((r ^ x0) & ~(R - 1)) + ((uint64_t)e & (R - 1));
                 const int xl = (int)((r ^ c) - x0);
                 const int kl = (int)(c - k0);
-                const uint64_t gi = r * N + c;
+                const uint64_t gi = (r & row_mask) * N + c;
                 dst[u] = sm.idx((xl << log_l) + kl);
                 if (in_bounds(st, gi, lim)) v[u] = io<InT>::template ld<T>(A + gi);
             }

@@ -129,6 +129,45 @@ def autotune(op: str, inp: torch.Tensor, out: torch.Tensor, precision: str, work
             "threads": p.threads, "ms": p.ms}
 
 
+def decompose_matrix_free(fill, n: int, a_dtype=torch.complex64, precision: str = "fp32", out_dtype=None,
+                          device=None) -> torch.Tensor:
+    """Decomposition of a 2^n x 2^n matrix that is never stored (Sec. V.B).
+
+    ``fill(xt, a, S)`` must write into the CUDA tensor S (shape (2^a, 2^n), dtype
+    a_dtype) the sheared tile set of x-block xt: S[i, k] = A[((k >> a) ^ xt) * 2^a + i, k],
+    on the current stream.  Returns C[x, z]."""
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    if out_dtype is None:
+        out_dtype = torch.complex128 if precision == "fp64" else torch.complex64
+    lib = _lib.load()
+    wsz = ctypes.c_size_t(0)
+    check(lib.ptdr_matrix_free_workspace_size(n, _dtype_code(a_dtype), _dtype_code(out_dtype), _prec(precision),
+                                              ctypes.byref(wsz)), "ptdr_matrix_free_workspace_size")
+    ws = torch.empty(wsz.value, dtype=torch.uint8, device=dev)
+    a = min(7, n)
+    S = ws[: (1 << (a + n)) * torch.empty((), dtype=a_dtype).element_size()].view(a_dtype).view(1 << a, 1 << n)
+    C = torch.empty((1 << n, 1 << n), dtype=out_dtype, device=dev)
+    errors = []
+
+    def cb(_user, n_, xt, a_, d_s, _stream):
+        try:
+            assert d_s == S.data_ptr() and a_ == a and n_ == n
+            fill(int(xt), a, S)
+            return 0
+        except Exception as exc:  # reported after the call
+            errors.append(exc)
+            return 1
+
+    fn = _lib.TILE_FN(cb)
+    st = lib.ptdr_decompose_matrix_free(n, _dtype_code(a_dtype), ctypes.cast(fn, ctypes.c_void_p), None,
+                                        ctypes.c_void_p(C.data_ptr()), _dtype_code(out_dtype), _prec(precision),
+                                        ctypes.c_void_p(ws.data_ptr()), wsz.value, _stream(dev))
+    if errors:
+        raise errors[0]
+    check(st, "ptdr_decompose_matrix_free")
+    return C
+
+
 def host_scratch_size(n: int, a_dtype, c_dtype, precision: str) -> int:
     """Device scratch bytes that decompose_host needs (two A, two C buffers, workspace)."""
     out = ctypes.c_size_t(0)

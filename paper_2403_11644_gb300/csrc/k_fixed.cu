@@ -61,20 +61,16 @@ namespace {
 
 template <typename InT> struct in_of;
 template <> struct in_of<float2> {
-    static constexpr int bias = 127;
     __device__ static __forceinline__ fx2 cvt(float2 v, int S) { return fx2{fixed_of(v.x, S), fixed_of(v.y, S)}; }
 };
 template <> struct in_of<double2> {
-    static constexpr int bias = 1023;
     __device__ static __forceinline__ fx2 cvt(double2 v, int S) { return fx2{fixed_of(v.x, S), fixed_of(v.y, S)}; }
 };
 // real inputs (a real matrix, or real coefficients of a Hermitian matrix)
 template <> struct in_of<float> {
-    static constexpr int bias = 127;
     __device__ static __forceinline__ fx2 cvt(float v, int S) { return fx2{fixed_of(v, S), 0}; }
 };
 template <> struct in_of<double> {
-    static constexpr int bias = 1023;
     __device__ static __forceinline__ fx2 cvt(double v, int S) { return fx2{fixed_of(v, S), 0}; }
 };
 

@@ -14,15 +14,16 @@
 //     permuted by XOR with m) and (-1)^{|zl & (m ^ xl)|} =
 //     (-1)^{|zl & m|} (-1)^{|zl & xl|},
 //       sum_cl (-1)^{|zl & cl|} T[cl ^ xl][cl] = (-1)^{|zl & xl|} (H U)[zl][xl];
-//     the staging row receives S[xl][128 cb + zl] = i^{|zl & xl|} (H U)[zl][xl];
-//   row job (x):  c_x[128 zb + zl] = (-i)^{|xt & zb|} (H B)[zb][zl],
+//     the staging row receives S[xl][128 cb + zl] = (H U)[zl][xl];
+//   row job (x):  c_x[128 zb + zl] = (-i)^{|xt & zb|} i^{|xl & zl|} (H B)[zb][zl],
 //     B[cb][zl] = S[xl][128 cb + zl].
 // The phase of the definition, (-i)^{|x & z|} with |x & z| = |xt & zb| +
 // |xl & zl|, times the sign (-1)^{|zl & xl|} of the tile stage is
-// (-i)^{|xt & zb|} i^{|xl & zl|}: the factor that depends on (xl, zl) is
-// applied where each thread holds one zl and a run of xl (tile epilogue), the
-// factor that depends on zb alone where it is the same for a whole warp (row
-// epilogue).
+// (-i)^{|xt & zb|} i^{|xl & zl|}.  Both factors are applied once, after the
+// row stage (which is linear over cb, so a factor of zl commutes with it): in
+// the row epilogue each thread holds one zl, so i^{|xl & zl|} is a constant
+// added to the 2-bit exponent of the zb factor, which is the same for a whole
+// warp's run of zb.  The tile epilogue stores the products as they are.
 //
 // Each job is one tcgen05 product accumulated in float32 in tensor memory
 // (K = 128, taken in 4 chunks of 32).  Tile jobs: D = H U, M = zl, N = 256
@@ -38,20 +39,20 @@
 // exact in bf16.
 //
 // One persistent CTA per SM, warp-specialised, every hand-off an mbarrier:
-//   warp 17     producer: takes jobs from the queue and copies each K chunk
+//   warp 25     producer: takes jobs from the queue and copies each K chunk
 //               (32 rows of 1 KiB: tile rows from HBM, staging rows from L2)
 //               into a 3-deep raw ring with eight tensor-map copies of
 //               32 rows x 128 bytes (128-byte swizzle), which the copy engine
 //               serves at over twice the rate of 1 KiB row copies;
-//   warps 0-7   loaders: one raw row per lane (tile jobs read each complex
+//   warps 0-15  loaders: one raw row per lane (tile jobs read each complex
 //               value at its XOR-permuted column; the swizzle keeps the eight
 //               rows of a read phase on distinct banks), the split, and
 //               16-byte stores into the MN-major core matrices of a 2-deep
 //               operand ring;
-//   warp 16     one lane issues the MMAs of each chunk and commits the chunk
+//   warp 24     one lane issues the MMAs of each chunk and commits the chunk
 //               back to the ring and each job to one of two tensor-memory
 //               accumulators (2 x 256 columns);
-//   warps 8-15  epilogue: tcgen05.ld of the accumulator, phase, coalesced
+//   warps 16-23 epilogue: tcgen05.ld of the accumulator, phase, coalesced
 //               stores.
 // So the copies of one job, the split of the next chunk, the MMAs and the
 // epilogue of the job before overlap on each SM.
@@ -61,7 +62,7 @@
 // rounds of slack, so that a row job rarely finds its x-tile unfinished).  A
 // row job waits (bounded) until its x-tile's tile jobs are done; a tile job
 // waits (bounded) before writing its staging slot until the row jobs of the
-// x-tile that used the slot before are done.  A publisher warp (warp 18)
+// x-tile that used the slot before are done.  A publisher warp (warp 26)
 // counts each finished job once, after one fence, so that the epilogue warps
 // never wait for their own stores to drain.  Within a CTA
 // every stage waits only on older jobs, so the earliest unfinished job can
@@ -84,12 +85,14 @@ constexpr int kLog = 14;
 constexpr int kN = 1 << kLog;
 constexpr int kT = 128;
 constexpr int kTiles = kN / kT;
-constexpr int kLoadWarps = 8;
+constexpr int kLoadWarps = 16;
+constexpr int kGroupsPerWarp = 32 / kLoadWarps; // tile jobs: groups of 4 complex per loader thread and chunk
+constexpr int kUnitsPerWarp = 16 / kLoadWarps;  // row jobs: units of 8 zl per loader thread and chunk
 constexpr int kEpiWarps = 8;
-constexpr int kMmaWarp = kLoadWarps + kEpiWarps; // 16
+constexpr int kMmaWarp = kLoadWarps + kEpiWarps; // 24
 constexpr int kProdWarp = kMmaWarp + 1;          // 17
 constexpr int kPubWarp = kProdWarp + 1;          // 18
-constexpr int kThreads = (kPubWarp + 1) * 32;    // 608
+constexpr int kThreads = (kPubWarp + 1) * 32;    // 864
 constexpr int kChunks = 4;                        // K chunks of 32 rows per job
 constexpr uint32_t kSplitBytes = 32u * 256u * 2u; // one split of a chunk: 32 K x 256 M/N bf16
 constexpr uint32_t kChunkSmem = 3u * kSplitBytes; // 48 KiB operand chunk
@@ -490,28 +493,28 @@ __global__ void __launch_bounds__(kThreads, 1)
                 int xt = 0, xl = 0;
                 if (!stop) (void)decode(job, tile, xt, xl);
                 const uint32_t rrow = rawb_a + rs * kRawSlotBytes + 128u * (uint32_t)ml;
-                uint32_t w[48];
-                // all 16 shared loads of the chunk first, then the splits
-                float f[32];
+                uint32_t w[12 * kGroupsPerWarp];
+                // all shared loads of the chunk first, then the splits
+                float f[8 * kGroupsPerWarp];
                 if (!stop && tile) {
                     const int mh = (32 * c + ml) >> 2;
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const uint32_t A = (uint32_t)((4 * warp + i) ^ mh);
+                    for (int i = 0; i < kGroupsPerWarp; ++i) {
+                        const uint32_t A = (uint32_t)((kGroupsPerWarp * warp + i) ^ mh);
                         const uint32_t gb = rrow + 4096u * (A >> 2) + (((2u * (A & 3u)) ^ (sw & 6u)) << 4);
 #pragma unroll
                         for (int j = 0; j < 4; ++j)
                             lds64(gb + (e0 ^ (uint32_t)(((j >> 1) << 4) | ((j & 1) << 3))), f[8 * i + 2 * j], f[8 * i + 2 * j + 1]);
                     }
 #pragma unroll
-                    for (int i = 0; i < 4; ++i)
+                    for (int i = 0; i < kGroupsPerWarp; ++i)
 #pragma unroll
                         for (int k = 0; k < 4; ++k)
                             split3(f[8 * i + 2 * k], f[8 * i + 2 * k + 1], w[12 * i + k], w[12 * i + 4 + k], w[12 * i + 8 + k]);
                 } else if (!stop) {
 #pragma unroll
-                    for (int u = 0; u < 2; ++u) {
-                        const uint32_t v = (uint32_t)(2 * warp + u);
+                    for (int u = 0; u < kUnitsPerWarp; ++u) {
+                        const uint32_t v = (uint32_t)(kUnitsPerWarp * warp + u);
                         const uint32_t vb = rrow + 4096u * (v >> 1);
 #pragma unroll
                         for (int k = 0; k < 4; ++k) // re0, im0, re1, im1, ...
@@ -519,7 +522,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                                    f[16 * u + 4 * k + 2], f[16 * u + 4 * k + 3]);
                     }
 #pragma unroll
-                    for (int u = 0; u < 2; ++u)
+                    for (int u = 0; u < kUnitsPerWarp; ++u)
 #pragma unroll
                         for (int k = 0; k < 4; ++k) {
                             split3(f[16 * u + 4 * k], f[16 * u + 4 * k + 2], w[24 * u + k], w[24 * u + 4 + k], w[24 * u + 8 + k]);
@@ -538,8 +541,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint32_t slot = op_a + os * kChunkSmem + (uint32_t)(ml >> 3) * 4096u + (uint32_t)(ml & 7) * 16u;
                 if (!stop && tile) {
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const uint32_t at = slot + (uint32_t)(4 * warp + i) * 128u;
+                    for (int i = 0; i < kGroupsPerWarp; ++i) {
+                        const uint32_t at = slot + (uint32_t)(kGroupsPerWarp * warp + i) * 128u;
 #pragma unroll
                         for (int s = 0; s < 3; ++s)
                             sts128(at + (uint32_t)s * kSplitBytes, w[12 * i + 4 * s], w[12 * i + 4 * s + 1],
@@ -547,8 +550,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                 } else if (!stop) {
 #pragma unroll
-                    for (int u = 0; u < 2; ++u) {
-                        const uint32_t at = slot + (uint32_t)(2 * warp + u) * 128u;
+                    for (int u = 0; u < kUnitsPerWarp; ++u) {
+                        const uint32_t at = slot + (uint32_t)(kUnitsPerWarp * warp + u) * 128u;
 #pragma unroll
                         for (int s = 0; s < 3; ++s) {
                             sts128(at + (uint32_t)s * kSplitBytes, w[24 * u + 4 * s], w[24 * u + 4 * s + 1],
@@ -558,11 +561,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                         }
                     }
                     // the chunk's 32 staging rows are consumed: drop their 256 lines
-                    // from L2 without write-back (one per loader thread)
+                    // from L2 without write-back (one per loader thread of the first 256)
                     const int ln = 32 * warp + lane;
                     const float2* pl =
                         tab.stage + ((size_t)(xt % kSlots) * kT + xl) * kN + (size_t)(32 * c + (ln >> 3)) * kT + 16 * (ln & 7);
-                    asm volatile("discard.global.L2 [%0], 128;" ::"l"(pl) : "memory");
+                    if (ln < 256) asm volatile("discard.global.L2 [%0], 128;" ::"l"(pl) : "memory");
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncwarp();
@@ -581,18 +584,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         // lanes its warp slot may access) and accumulator columns of half h = e >> 2.
         const int q = warp & 3, hcol = (warp - kLoadWarps) >> 2;
         const int zl = 32 * q + lane;
-        // Tile jobs: i^{|xl & zl|} for this thread's zl and the 64 xl = 64 h + k of its
-        // columns; bit k & 31 of word k >> 5 in three masks: odd power (re/im swap),
-        // sign of the real part (power 1, 2), sign of the imaginary part (power 2, 3).
-        uint32_t t_odd[2] = {0u, 0u}, t_sx[2] = {0u, 0u}, t_sy[2] = {0u, 0u};
-#pragma unroll
-        for (int k = 0; k < 64; ++k) {
-            const uint32_t ph = (uint32_t)__popc((64 * hcol + k) & zl) & 3u;
-            const uint32_t bit = 1u << (k & 31);
-            t_odd[k >> 5] |= (ph & 1u) ? bit : 0u;
-            t_sx[k >> 5] |= ((ph ^ (ph >> 1)) & 1u) ? bit : 0u;
-            t_sy[k >> 5] |= (ph & 2u) ? bit : 0u;
-        }
         for (uint32_t J = 0;; ++J) {
             const uint32_t b = J & 1;
             int job = -1;
@@ -651,19 +642,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                         __syncwarp();
                         if (lane == 0) mbar_arrive(su32(&t_empty[b]));
                     }
-                    // this run's 16 bits of the tables, moved to bits 0..15
-                    const int sh = 16 * (cc & 1);
-                    const uint32_t od = (cc & 2 ? t_odd[1] : t_odd[0]) >> sh;
-                    const uint32_t sx = (cc & 2 ? t_sx[1] : t_sx[0]) >> sh;
-                    const uint32_t sy = (cc & 2 ? t_sy[1] : t_sy[0]) >> sh;
+                    // the product as it is: the phase is applied after the row stage
                     float2* srow = stage + (size_t)(16 * cc) * kN;
 #pragma unroll
-                    for (int u = 0; u < 16; ++u) {
-                        const bool odd = ((od >> u) & 1u) != 0;
-                        const uint32_t ox = (odd ? v[2 * u + 1] : v[2 * u]) ^ sgn(sx, u);
-                        const uint32_t oy = (odd ? v[2 * u] : v[2 * u + 1]) ^ sgn(sy, u);
-                        __stcg(srow + (size_t)u * kN, make_float2(__uint_as_float(ox), __uint_as_float(oy)));
-                    }
+                    for (int u = 0; u < 16; ++u)
+                        __stcg(srow + (size_t)u * kN, make_float2(__uint_as_float(v[2 * u]), __uint_as_float(v[2 * u + 1])));
                 }
             } else {
                 // real parts of zl in columns zb, imaginary parts in 128 + zb;
@@ -685,8 +668,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                 float2* out = (float2*)Cv + o0;
                 float* outr = (float*)Cv + o0;
 #pragma unroll
+                // the tile stage's factor i^{|xl & zl|} = (-i)^{3 |xl & zl|} is constant for
+                // this thread's zl (the row stage is linear over cb, so it commutes)
+                const uint32_t c_l = (3u * (uint32_t)__popc(xl & zl)) & 3u;
                 for (int cc = 0; cc < 2; ++cc) {
-                    const uint32_t bs = (uint32_t)__popc(xt & (64 * hcol + 32 * cc)) & 3u;
+                    const uint32_t bs = ((uint32_t)__popc(xt & (64 * hcol + 32 * cc)) + c_l) & 3u;
                     const uint32_t odd = w1 ^ ((bs & 1u) ? 0xFFFFFFFFu : 0u);
                     const uint32_t two = w2 ^ ((bs & 2u) ? 0xFFFFFFFFu : 0u) ^ ((bs & 1u) ? w1 : 0u);
                     const uint32_t sx = two, sy = odd ^ two;

@@ -135,29 +135,29 @@ __device__ void load_gather(cplx_t<T>* s, const Smem& sm, const InT* A, int n, u
             }
         }
         asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
-        return;
-    }
-    for (int e0 = threadIdx.x; e0 < E; e0 += kLoadBatch * blockDim.x) {
-        cplx_t<T> v[kLoadBatch];
-        int dst[kLoadBatch];
+    } else {
+        for (int e0 = threadIdx.x; e0 < E; e0 += kLoadBatch * blockDim.x) {
+            cplx_t<T> v[kLoadBatch];
+            int dst[kLoadBatch];
 #pragma unroll
-        for (int u = 0; u < kLoadBatch; ++u) {
-            const int e = e0 + u * blockDim.x;
-            dst[u] = -1;
-            v[u] = mk<T>(0, 0);
-            if (e < E) {
-                const uint64_t r = rb + ((uint64_t)e >> log_r);
-                const uint64_t c = ((r ^ x0) & ~(R - 1)) + ((uint64_t)e & (R - 1));
-                const int xl = (int)((r ^ c) - x0);
-                const int kl = (int)(c - k0);
-                const uint64_t gi = (r & row_mask) * N + c;
-                dst[u] = sm.idx((xl << log_l) + kl);
-                if (in_bounds(st, gi, lim)) v[u] = io<InT>::template ld<T>(A + gi);
+            for (int u = 0; u < kLoadBatch; ++u) {
+                const int e = e0 + u * blockDim.x;
+                dst[u] = -1;
+                v[u] = mk<T>(0, 0);
+                if (e < E) {
+                    const uint64_t r = rb + ((uint64_t)e >> log_r);
+                    const uint64_t c = ((r ^ x0) & ~(R - 1)) + ((uint64_t)e & (R - 1));
+                    const int xl = (int)((r ^ c) - x0);
+                    const int kl = (int)(c - k0);
+                    const uint64_t gi = (r & row_mask) * N + c;
+                    dst[u] = sm.idx((xl << log_l) + kl);
+                    if (in_bounds(st, gi, lim)) v[u] = io<InT>::template ld<T>(A + gi);
+                }
             }
-        }
 #pragma unroll
-        for (int u = 0; u < kLoadBatch; ++u)
-            if (dst[u] >= 0) s[dst[u]] = v[u];
+            for (int u = 0; u < kLoadBatch; ++u)
+                if (dst[u] >= 0) s[dst[u]] = v[u];
+        }
     }
 }
 

@@ -34,14 +34,14 @@ METRIC = "Pauli coeffs/s and HBM GB/s at n=14, split-BF16 TC vs FP64 plain"
 # path, from one ncu capture each (summaries under profiles/).  A figure is
 # reported only while the sources it was taken from are unchanged.
 NCU_TRAFFIC = {
-    "fp32": {"kernel": "k_dense14_staged", "bytes": 2_157_630_720 + 2_158_184_448,
+    "fp32": {"kernel": "k_dense_staged", "bytes": 2_158_049_280 + 2_157_005_824,
              "sources": {"paper_2403_11644_gb300/csrc/k_dense14s.cu":
-                         "0ca9f8674df9a8b43490c448728f48d96a7bc33a9cbd206e4409619055ad01be",
+                         "f594787dd5a28f96f4936cba21eb9c3ce66a261f694b1cd2e89fbdf8b9658b1b",
                          "paper_2403_11644_gb300/csrc/common.cuh":
                          "0b8af7566a7fe16e8503406413c2ad8e3700521db352a206df357200a0645186"}},
-    "bf16x3": {"kernel": "k_tc14_pipe", "bytes": 2_148_264_704 + 2_102_129_152,
+    "bf16x3": {"kernel": "k_tc14_pipe", "bytes": 2_148_109_056 + 2_117_101_056,
                "sources": {"paper_2403_11644_gb300/csrc/k_tc14p.cu":
-                           "4e6af00cdcfa9d761b706c7fa8d5ff3947371bc37724b93ff7003df1dc99dc4f",
+                           "73bfacd58afdf0c55982c9debede00e63df09eac46fdfd6995f02a1cfad12e0e",
                            "paper_2403_11644_gb300/csrc/common.cuh":
                            "0b8af7566a7fe16e8503406413c2ad8e3700521db352a206df357200a0645186"}},
 }
@@ -52,7 +52,7 @@ def ncu_traffic(prec, n):
     import hashlib
     e = NCU_TRAFFIC.get(prec)
     if e is None or n != 14:
-        return ({"bf16x3": "k_tc14_pipe"}.get(prec) if n == 14 else None), None
+        return ({"bf16x3": "k_tc14_pipe", "fp32": "k_dense_staged"}.get(prec) if n == 14 else None), None
     for rel, sha in e["sources"].items():
         path = os.path.join(ROOT, rel)
         if not os.path.exists(path):

@@ -254,27 +254,40 @@ def job_throughput(total_ms: float, steps: int, units_per_rank: int, world: int,
     return ms, world * units_per_rank / (ms * 1e-3)
 
 
-def host_link_gbs(h_in, h_out, d_in, d_out, dev, reps=3):
-    """GB/s each way of plain copies host -> device and device -> host run at
-    the same time on two streams: the bound of the host-buffer path, whose
-    every step moves its input in and its output out."""
+def host_link(h_in, h_out, d_in, d_out, dev, reps=3):
+    """The host link as the host-buffer path sees it: ms per copy of the input
+    alone (host -> device), of the output alone (device -> host), and of both at
+    the same time on two streams, plus the GB/s each way of the last.  A step of
+    the host-buffer path moves its input in and its output out, so its bound is
+    the time of both at once; if a run takes the sum of the two alone instead,
+    the two directions did not overlap."""
     import torch
     up, down = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
 
-    def both():
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize(dev)
+        t = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize(dev)
+        return (time.perf_counter() - t) * 1e3 / reps
+
+    def up_only():
         with torch.cuda.stream(up):
             d_in.copy_(h_in, non_blocking=True)
+
+    def down_only():
         with torch.cuda.stream(down):
             h_out.copy_(d_out, non_blocking=True)
 
-    both()
-    torch.cuda.synchronize(dev)
-    t = time.perf_counter()
-    for _ in range(reps):
-        both()
-    torch.cuda.synchronize(dev)
-    sec = time.perf_counter() - t
-    return reps * min(h_in.numel() * h_in.element_size(), h_out.numel() * h_out.element_size()) / sec / 1e9
+    def both():
+        up_only()
+        down_only()
+
+    ms_up, ms_down, ms_both = timed(up_only), timed(down_only), timed(both)
+    nbytes = min(h_in.numel() * h_in.element_size(), h_out.numel() * h_out.element_size())
+    return {"up_ms": ms_up, "down_ms": ms_down, "both_ms": ms_both, "gbs_each_way": nbytes / (ms_both * 1e-3) / 1e9}
 
 
 def parse():
@@ -594,7 +607,7 @@ def main():
         A_pin = torch.from_numpy(A_h).pin_memory()
         C_pins = [torch.empty(C.shape, dtype=C.dtype).pin_memory() for _ in range(2)]
         # the host link this process sees (A is rewritten with its own values)
-        link = host_link_gbs(A_pin, C_pins[0], A, C, dev)
+        link = host_link(A_pin, C_pins[0], A, C, dev)
         e2e_steps = max(3, min(args.steps, 20))  # the first upload and the last download are not overlapped
         scratch = torch.empty(ptdr.host_scratch_size(N_QUBITS, A.dtype, out_dtype, prec), dtype=torch.uint8,
                               device=dev)
@@ -614,8 +627,10 @@ def main():
             result["e2e"] = {"value": e_value, "unit": "coeffs/s",
                              "h2d_bytes_per_step": in_b, "d2h_bytes_per_step": out_b,
                              "ms_per_step": e_ms, "steps": e2e_steps,
-                             "link_gbs_each_way": link,
-                             "link_bound_ms_per_step": max(in_b, out_b) / (link * 1e9) * 1e3,
+                             "link_gbs_each_way": link["gbs_each_way"],
+                             "link_bound_ms_per_step": link["both_ms"],
+                             "link_up_alone_ms": link["up_ms"], "link_down_alone_ms": link["down_ms"],
+                             "link_serial_ms_per_step": link["up_ms"] + link["down_ms"],
                              "api": "ptdr_decompose_host (C ABI, host buffers, transfers overlapped across steps)"}
         del scratch
 

@@ -17,7 +17,7 @@
 //            runs).  The consumed staging lines are discarded from L2.
 // HBM sees C read once and A written once, in whole 512-byte runs.
 //
-// One persistent kernel (2 CTAs of 256 threads per SM) takes items from an
+// One persistent kernel (3 CTAs of 256 threads per SM) takes items from an
 // atomic queue in x-tile-major rounds: round r holds the 256 half-row items of
 // x-tile r, then the 256 half-tile items of x-tile r - 1.  A half-tile item
 // waits (bounded) until its x-tile's 256 half-row items are done; a half-row
@@ -99,7 +99,7 @@ struct ComposeTables {
     unsigned long long wait_ns; // bound of every wait for another CTA
 };
 
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, 3)
     k_compose14_staged(const float2* __restrict__ C, float2* __restrict__ A, float scale, ComposeTables tab,
                        unsigned int* st)
 {
@@ -184,17 +184,24 @@ __global__ void __launch_bounds__(kThreads, 2)
             if (t == 0) wait_count(tab.done1 + xt, kDone, tab.wait_ns, st);
             __syncthreads();
             const int R = cb ^ xt;
-            // staging rows xl = 64 h + xloc, columns 128 cb .. 128 cb + 127 -> buf[xloc][zl]
+            // staging rows xl = 64 h + row, columns 128 cb .. 128 cb + 127, straight into
+            // registers (coalesced 256-byte L2 reads, 32 in flight per thread): thread =
+            // (row 8 w + i, zl bits 0-4 = lane); zl bits 5-6 transformed there, then buf[row][zl]
             const float2* sblk = tab.stage + ((size_t)(xt % kSlots) * kT + kH * h) * kN + (size_t)kT * cb;
-            const uint32_t tbuf_a = (uint32_t)__cvta_generic_to_shared(buf);
+            {
+                float2 e[8][4];
 #pragma unroll
-            for (int i = 0; i < 32; ++i) {
-                const int e = t + kThreads * i; // 8192 values: row e >> 7, zl e & 127
-                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(tbuf_a + 8u * (uint32_t)((e >> 7) * kTileStride + (e & 127))),
-                             "l"(sblk + (size_t)(e >> 7) * kN + (e & 127))
-                             : "memory");
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int gg = 0; gg < 4; ++gg)
+                        e[i][gg] = __ldcg(sblk + (size_t)(8 * warp + i) * kN + 32 * gg + lane);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    wht_regs<2>(e[i]);
+#pragma unroll
+                    for (int gg = 0; gg < 4; ++gg) buf[(8 * warp + i) * kTileStride + 32 * gg + lane] = e[i][gg];
+                }
             }
-            asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
             __syncthreads();
             // the 64 staging rows of this block are consumed: drop their lines from L2
 #pragma unroll
@@ -203,18 +210,6 @@ __global__ void __launch_bounds__(kThreads, 2)
                 const float2* p = sblk + (size_t)(ln >> 3) * kN + 16 * (ln & 7);
                 asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
             }
-            // zl bits 5-6 in place: thread = (row 8 w + i, zl bits 0-4 = lane)
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int row = 8 * warp + i;
-                float2 e[4];
-#pragma unroll
-                for (int gg = 0; gg < 4; ++gg) e[gg] = buf[row * kTileStride + 32 * gg + lane];
-                wht_regs<2>(e);
-#pragma unroll
-                for (int gg = 0; gg < 4; ++gg) buf[row * kTileStride + 32 * gg + lane] = e[gg];
-            }
-            __syncthreads();
             // zl bits 0-4 in registers: thread = (mask xloc = 32 (w & 1) + l, group g = w >> 1).
             // Multiplying input s by (-1)^{|l & s|} before the transform leaves register c
             // holding output cl = 32 g + (c ^ l), so that for each c the 32 lanes of the warp

@@ -2,7 +2,7 @@
 // arithmetic, as two passes over an L2-resident staging buffer with
 // contiguous HBM traffic.  (Written out below for n = 14; at n = 15 the
 // transform across column blocks has 8 bits, as a 5-bit and a 3-bit register
-// round, row items cover 32 of a mask's 128 z_lo values, and two staging
+// round, row items cover 32 of a mask's 128 z_lo values, and three staging
 // slots of 32 MiB replace four of 16 MiB.)
 //
 // The XOR shear d_x[k] = A[k ^ x][k] maps 128 x 128 tiles onto 128 x 128
@@ -30,7 +30,7 @@
 // 256 half-tile items of x-tile r, then the 256 half-row items of x-tile r-1.
 // A half-row item waits (bounded) until its x-tile's 256 half-tile items are
 // done; a half-tile item of x-tile c waits (bounded) before writing until
-// x-tile c-2 has been read out of the same staging slot.  Every item waited
+// x-tile c - kSlots has been read out of the same staging slot.  Every item waited
 // on was dequeued earlier by a running CTA, so the waits always end.
 #include <mutex>
 
@@ -63,7 +63,7 @@ template <int LOG> struct Geo {
     static constexpr int kRowItems = kT * (kT / kZl);
     static constexpr int kPerRound = kTileItems + kRowItems;
     static constexpr int kItems = (kTiles + 1) * kPerRound;
-    static constexpr int kSlots = LOG == 14 ? 4 : 2; // staging slots: 64 MiB of L2 either way
+    static constexpr int kSlots = LOG == 14 ? 4 : 3; // staging slots: 64 MiB (n = 14), 96 MiB (n = 15) of L2
     static_assert((1 << kCbBits) * kYb <= kSmemElems, "row item fits the shared buffer");
 };
 
@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(kThreads, 2)
 size_t dense_staged_workspace(int n)
 {
     // counters (head, done1[x-tiles], done2[x-tiles]) padded to 4 KiB, then the slots:
-    // 4 x 16 MiB at n = 14, 2 x 32 MiB at n = 15
+    // 4 x 16 MiB at n = 14, 3 x 32 MiB at n = 15
     return n == 14 ? 4096 + (size_t)Geo<14>::kSlots * kT * Geo<14>::kN * sizeof(float2)
                    : 4096 + (size_t)Geo<15>::kSlots * kT * Geo<15>::kN * sizeof(float2);
 }

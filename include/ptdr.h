@@ -280,9 +280,9 @@ ptdr_status ptdr_batched_workspace_size(const int* h_n, int count, ptdr_dtype a_
  * library convenience, not part of the method.
  *
  * Who needs it: an application that embeds this library but owns all device
- * memory through its own pool, code that runs during a CUDA graph capture or
- * on a latency-critical stream where an allocation would synchronise the
- * device, or a runtime that forbids allocations after start-up.  Such a caller
+ * memory through its own pool, code on a latency-critical stream where an
+ * allocation would synchronise the device, or a runtime that forbids
+ * allocations after start-up.  Such a caller
  * cannot provide the workspace ptdr_decompose_batched asks for.  This variant
  * allocates nothing: its scratch is a fixed 32,784-byte array in the library's
  * device image (every GPU that loads the library holds it until exit).
@@ -291,9 +291,9 @@ ptdr_status ptdr_batched_workspace_size(const int* h_n, int count, ptdr_dtype a_
  *   count      at most 4096 matrices; larger batches return
  *              PTDR_ERR_WORKSPACE (use ptdr_decompose_batched instead).
  *   The first call on each device looks up the array's device address (with
- *   that device current) and caches it for the life of the process; make that
- *   first call before any stream capture, and do not use the library across a
- *   cudaDeviceReset (which reloads the array at a new address).  Every call shares the one array, which keeps the last
+ *   that device current) and caches it for the life of the process; do not use
+ *   the library across a cudaDeviceReset (which reloads the array at a new
+ *   address).  Every call shares the one array, which keeps the last
  *   call's tables; each call rewrites all of it (including the work-queue
  *   counter) before use, so results never depend on an earlier call, but two
  *   calls whose work overlaps on the GPU (different streams, or different

@@ -3,9 +3,8 @@
 //
 // Some callers cannot allocate device memory at the point where they want to
 // decompose: a host application whose device memory is entirely owned by its
-// own pool or allocator, code that runs under a CUDA graph capture or on a
-// latency-critical stream where an allocation would add a device-wide
-// synchronisation, or a runtime that forbids dynamic allocation after start-up.
+// own pool or allocator, code on a latency-critical stream where an
+// allocation would add a device-wide synchronisation, or a runtime that forbids dynamic allocation after start-up.
 // This entry point lets them run the batched decomposition with nothing but
 // their inputs and outputs: its only scratch (the planner's tables and the
 // work-queue counter) lives in a fixed array in the library's device image,

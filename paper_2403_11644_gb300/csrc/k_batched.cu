@@ -4,9 +4,9 @@
 // items are (matrix, block of masks) pairs taken from an atomic queue in
 // longest-first order, so a single grid of resident CTAs balances matrices
 // of n = 1..13 without a launch per matrix.  Items of complex64 matrices of
-// n = 9, 10, 11 computed in FP32 run the register-round items of
-// rr_items.cuh; every other item runs the generic tile path (gather,
-// shared-memory passes, phased write-out).
+// n = 9 .. 12 computed in FP32 run the register-round items of rr_items.cuh;
+// every other item runs the generic tile path (gather, shared-memory passes,
+// phased write-out).
 #include <algorithm>
 #include <type_traits>
 
@@ -99,11 +99,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_batched(BatchLa
         OutT* C = (OutT*)p.d_C[m];
         if constexpr (std::is_same<T, float>::value && std::is_same<InT, float2>::value &&
                       std::is_same<OutT, float2>::value) {
-            if (n >= 9 && n <= 11 && log_r == 13 - n && !(((uintptr_t)A | (uintptr_t)C) & 15)) {
+            if (n >= 9 && n <= 12 && log_r == 13 - n && !(((uintptr_t)A | (uintptr_t)C) & 15)) {
                 const float sc = ldexpf(1.0f, -n);
                 if (n == 9) rr_item<9>(A, C, (uint32_t)x0, s, sc, st);
                 else if (n == 10) rr_item<10>(A, C, (uint32_t)x0, s, sc, st);
-                else rr_item<11>(A, C, (uint32_t)x0, s, sc, st);
+                else if (n == 11) rr_item<11>(A, C, (uint32_t)x0, s, sc, st);
+                else rr_item<12>(A, C, (uint32_t)x0, s, sc, st);
                 __syncthreads(); // s and s_item are reused by the next item
                 continue;
             }

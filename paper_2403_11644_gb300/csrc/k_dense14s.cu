@@ -19,7 +19,9 @@
 //            with contiguous stores, and discard the staging lines so the
 //            dead intermediate is never written back to HBM.
 // HBM sees A read once and C written once, both in whole 1 KiB rows, instead
-// of 32-byte pieces from rows 128 KiB apart.
+// of 32-byte pieces from rows 128 KiB apart.  A is loaded with an L2
+// evict-first policy so that its lines, read once, leave L2 before the live
+// staging does (at n = 15 the staging fills 96 MiB of L2).
 //
 // Work items are halves (64 KiB each) so that two CTAs share an SM and one
 // CTA's loads overlap the other's arithmetic: a half-tile item covers 64 of
@@ -136,6 +138,8 @@ __global__ void __launch_bounds__(kThreads, 2)
     float2* buf = reinterpret_cast<float2*>(smem_raw + (buf_a - raw_a));
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const float scale = 1.0f / (float)kN;
+    uint64_t pol_a; // A is read once: its lines go first, ahead of live staging
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol_a));
 
     // thread 0 keeps the next item in hand so the queue's atomic latency
     // overlaps the current item (a held item is always later in the queue
@@ -167,7 +171,8 @@ __global__ void __launch_bounds__(kThreads, 2)
                 const int b = ((rl >> 6) ^ h) & 1;
                 const uint64_t gi = ((uint64_t)(kT * R + rl) << LOG) + (uint64_t)(kT * cb + kH * b) + 2u * (qc & 31);
                 const float2* src = A + (in_bounds(st, gi + 1, (uint64_t)kN * kN) ? gi : 0);
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(buf_a + (uint32_t)qc * 16u), "l"(src)
+                asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(buf_a + (uint32_t)qc * 16u),
+                             "l"(src), "l"(pol_a)
                              : "memory");
             }
             asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");

@@ -1,7 +1,7 @@
 // Register-round items: the decomposition of R = 2^(13-n) masks of one
 // complex64 matrix of n = 9 .. 12, computed in FP32 by one CTA of 256 threads
-// through one shared tile of 8192 values.  Used by the batched kernel (its
-// items of n = 9, 10, 11) and by the dense single-matrix launch (n = 9 .. 12).
+// through one shared tile of 8192 values.  Used by the batched kernel and by
+// the dense single-matrix launch.
 #pragma once
 
 #include <type_traits>

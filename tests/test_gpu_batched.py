@@ -64,10 +64,10 @@ def test_batched_graph_replay():
 
 
 def test_batched_fp32_unaligned_and_aligned_mixed():
-    """complex64 matrices of n = 9, 10, 11 whose A or C starts 8 bytes past a
+    """complex64 matrices of n = 9 .. 12 whose A or C starts 8 bytes past a
     16-byte boundary take the element-wise gather; aligned ones in the same
     launch take the 16-byte piece copies.  Both match the oracle."""
-    ns = [11, 10, 9, 11, 10, 9, 8]
+    ns = [11, 10, 9, 11, 10, 9, 8, 12, 12, 12]
     mats = [workloads.dense(n, 400 + i, dtype=np.complex64) for i, n in enumerate(ns)]
     As, Cs = [], []
     for i, m in enumerate(mats):

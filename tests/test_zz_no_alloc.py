@@ -1,8 +1,7 @@
 """ptdr_decompose_batched_static: the batched decomposition without a workspace.
 
 For callers that cannot allocate device memory (their memory is owned by their
-own pool, they run under graph capture, or allocation after start-up is not
-allowed), the library offers a variant whose scratch is a fixed array in its
+own pool, or allocation after start-up is not allowed), the library offers a variant whose scratch is a fixed array in its
 device image.  Its results must match the workspace entry point's, call after
 call, because every call rewrites the shared array before use.  Collected last
 on purpose (file name), so a failure here comes after every other test ran.

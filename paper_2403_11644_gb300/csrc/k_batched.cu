@@ -70,52 +70,177 @@ __global__ void k_batch_plan(const int* d_n, int count, BatchTables tab, int til
     tab.hdr[2] = r;            // ranked matrices
 }
 
+// One work item as the loop needs it: its queue index (>= total: no item),
+// matrix and first mask, and whether it runs the register rounds.
+struct BatchItem {
+    int item;
+    int n, log_r, rr;
+    uint64_t x0;
+    const void* A;
+    void* C;
+};
+
+// Warp 0's view of the queue, kept in shared memory (nothing of it stays in
+// registers across an item): the rank of the last resolved item (a CTA's
+// items only increase, so the rank never decreases), that rank's matrix, and
+// the queue index taken ahead of time (its atomic's latency overlaps an item).
+struct BatchCursor {
+    int rank, m, n, start, ahead;
+    const void* A;
+    void* C;
+};
+
+// Warp-collective (all 32 lanes of warp 0): resolves queue index `item`
+// against the cursor c; lane 0 updates c and returns the item.
+template <bool kRr>
+__device__ BatchItem resolve_item(BatchCursor* c, int item, const BatchLaunch& p, const BatchTables& tab, int total,
+                                  int ranked, int lane)
+{
+    BatchItem it{};
+    it.item = item;
+    if (item >= total) return it;
+    // rank = last r with start[r] <= item: probe the next 32 ranks at once
+    // (starts increase, so those <= item are a prefix), else binary search
+    int rank = c->rank;
+    const int r = rank + 1 + lane;
+    const int v = r < ranked ? tab.start[r] : 0x7fffffff;
+    const unsigned le = __ballot_sync(0xffffffffu, v <= item);
+    if (le != 0xffffffffu) {
+        rank += __popc(le);
+    } else {
+        int lo = rank + 32, hi = ranked - 1;
+        if (lane == 0)
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (tab.start[mid] <= item) lo = mid;
+                else hi = mid - 1;
+            }
+        rank = __shfl_sync(0xffffffffu, lo, 0);
+    }
+    if (lane == 0) {
+        const int m = tab.order[rank];
+        if (m != c->m) {
+            c->m = m;
+            c->start = tab.start[rank];
+            c->n = p.d_n[m];
+            c->A = p.d_A[m];
+            c->C = p.d_C[m];
+        }
+        c->rank = rank;
+        it.n = c->n;
+        it.log_r = batch_log_r(it.n, p.tile_log);
+        it.x0 = (uint64_t)(item - c->start) << it.log_r;
+        it.A = c->A;
+        it.C = c->C;
+        it.rr = kRr && it.n >= 9 && it.n <= 12 && it.log_r == 13 - it.n && !(((uintptr_t)it.A | (uintptr_t)it.C) & 15);
+    }
+    __syncwarp();
+    return it;
+}
+
+__device__ __forceinline__ void rr_issue_n(int n, const void* A, uint64_t x0, float2* s, unsigned int* st)
+{
+    const float2* a = (const float2*)A;
+    if (n == 9) rr_issue<9>(a, (uint32_t)x0, s, st);
+    else if (n == 10) rr_issue<10>(a, (uint32_t)x0, s, st);
+    else if (n == 11) rr_issue<11>(a, (uint32_t)x0, s, st);
+    else rr_issue<12>(a, (uint32_t)x0, s, st);
+}
+
+// The persistent loop.  Items pass through a ring of three shared slots: while
+// item i runs, item i + 1 is already resolved (its copies are issued by item
+// i's hook) and warp 0 resolves item i + 2 after item i's first round, so
+// that its dependent table loads overlap the other warps' second round
+// instead of holding every warp at a barrier.
 template <typename T, typename InT, typename OutT>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_batched(BatchLaunch p, BatchTables tab, unsigned int* st)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using T2 = cplx_t<T>;
     T2* s = reinterpret_cast<T2*>(smem_raw);
-    __shared__ int s_item;
+    __shared__ BatchItem s_it[3];
+    __shared__ BatchCursor s_cur;
+    constexpr bool kRr = std::is_same<T, float>::value && std::is_same<InT, float2>::value &&
+                         std::is_same<OutT, float2>::value;
     const int total = tab.hdr[1];
     const int ranked = tab.hdr[2];
-    for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(&tab.hdr[0], 1);
-        __syncthreads();
-        const int item = s_item;
-        if (item >= total) break;
-        // rank = last k with start[k] <= item
-        int lo = 0, hi = ranked - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (tab.start[mid] <= item) lo = mid;
-            else hi = mid - 1;
+    const int t = threadIdx.x, lane = t & 31;
+    // warp 0: resolves the queue index taken ahead into slot `to` and takes the next one
+    auto advance = [&](int to) {
+        const int q = s_cur.ahead;
+        int q2 = total;
+        if (lane == 0 && q < total) q2 = atomicAdd(&tab.hdr[0], 1);
+        const BatchItem nx = resolve_item<kRr>(&s_cur, q, p, tab, total, ranked, lane);
+        if (lane == 0) {
+            s_it[to] = nx;
+            s_cur.ahead = q2;
         }
-        const int m = tab.order[lo];
-        const int n = p.d_n[m];
-        const int log_r = batch_log_r(n, p.tile_log);
-        const uint64_t x0 = (uint64_t)(item - tab.start[lo]) << log_r;
-        const InT* A = (const InT*)p.d_A[m];
-        OutT* C = (OutT*)p.d_C[m];
-        if constexpr (std::is_same<T, float>::value && std::is_same<InT, float2>::value &&
-                      std::is_same<OutT, float2>::value) {
-            if (n >= 9 && n <= 12 && log_r == 13 - n && !(((uintptr_t)A | (uintptr_t)C) & 15)) {
-                const float sc = ldexpf(1.0f, -n);
-                if (n == 9) rr_item<9>(A, C, (uint32_t)x0, s, sc, st);
-                else if (n == 10) rr_item<10>(A, C, (uint32_t)x0, s, sc, st);
-                else if (n == 11) rr_item<11>(A, C, (uint32_t)x0, s, sc, st);
-                else rr_item<12>(A, C, (uint32_t)x0, s, sc, st);
-                __syncthreads(); // s and s_item are reused by the next item
+        __syncwarp();
+    };
+    if (t < 32) {
+        if (lane == 0) {
+            s_cur.rank = 0;
+            s_cur.m = -1;
+            s_cur.ahead = atomicAdd(&tab.hdr[0], 1);
+        }
+        __syncwarp();
+        advance(0);
+        advance(1);
+    }
+    __syncthreads();
+    int slot = 0;
+    bool issued = false; // the current item's piece copies are in flight
+    if constexpr (kRr) {
+        const BatchItem it = s_it[0];
+        if (it.item < total && it.rr) {
+            rr_issue_n(it.n, it.A, it.x0, reinterpret_cast<float2*>(s), st);
+            issued = true;
+        }
+    }
+    for (;;) {
+        const BatchItem it = s_it[slot];
+        if (it.item >= total) break;
+        const int s1 = slot == 2 ? 0 : slot + 1, s2 = s1 == 2 ? 0 : s1 + 1;
+        if constexpr (kRr) {
+            if (it.rr) {
+                float2* sf = reinterpret_cast<float2*>(s);
+                bool next_issued = false;
+                // after round 1 (warp 0): resolve the item after next; once the last
+                // round has read the tile: the next item's copies
+                auto mid = [&]() {
+                    if (t < 32) advance(s2);
+                };
+                auto hook = [&]() {
+                    __syncthreads();
+                    const BatchItem nx = s_it[s1];
+                    if (nx.item < total && nx.rr) {
+                        rr_issue_n(nx.n, nx.A, nx.x0, sf, st);
+                        next_issued = true;
+                    }
+                };
+                const float2* A = (const float2*)it.A;
+                float2* C = (float2*)it.C;
+                const float sc = ldexpf(1.0f, -it.n);
+                if (it.n == 9) rr_item<9>(A, C, (uint32_t)it.x0, sf, sc, st, issued, hook, mid);
+                else if (it.n == 10) rr_item<10>(A, C, (uint32_t)it.x0, sf, sc, st, issued, hook, mid);
+                else if (it.n == 11) rr_item<11>(A, C, (uint32_t)it.x0, sf, sc, st, issued, hook, mid);
+                else rr_item<12>(A, C, (uint32_t)it.x0, sf, sc, st, issued, hook, mid);
+                __syncthreads(); // s_it[s2] is complete; s is rewritten next
+                issued = next_issued;
+                slot = s1;
                 continue;
             }
         }
-        const Smem sm = make_smem(n);
-        const uint64_t elems = 1ull << (2 * n);
-        load_gather<T>(s, sm, A, n, x0, log_r, 0, n, elems, st);
+        if (t < 32) advance(s2);
+        const Smem sm = make_smem(it.n);
+        const uint64_t elems = 1ull << (2 * it.n);
+        load_gather<T>(s, sm, (const InT*)it.A, it.n, it.x0, it.log_r, 0, it.n, elems, st);
         __syncthreads();
-        wht_bits(s, sm, log_r + n, 0, n);
-        store_row_phase<T>(C, s, sm, n, x0, log_r, 0, n, 0, (T)ldexp(1.0, -n), elems, st);
-        __syncthreads(); // s and s_item are reused by the next item
+        wht_bits(s, sm, it.log_r + it.n, 0, it.n);
+        store_row_phase<T>((OutT*)it.C, s, sm, it.n, it.x0, it.log_r, 0, it.n, 0, (T)ldexp(1.0, -it.n), elems, st);
+        __syncthreads(); // s is reused next
+        issued = false;
+        slot = s1;
     }
 }
 

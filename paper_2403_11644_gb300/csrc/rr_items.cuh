@@ -73,17 +73,17 @@ __device__ __forceinline__ void rr_put(float2* C, uint32_t x, uint32_t z, int sg
     *reinterpret_cast<float4*>(C + z) = make_float4(pa.x, pa.y, pb.x, pb.y);
 }
 
+// Issues (one commit group, not waited for) the 16-byte copies of item x0's
+// piece tile: row r of A, columns ((r ^ x0) & ~(R - 1)) + [0, R), at s[r R].
+// 4096 value pairs, 16 per thread: pair q is row q >> (lr - 1), columns
+// ((r ^ x0) & ~(R - 1)) + 2 (q & (R / 2 - 1)) + {0, 1}, tile values 2q, 2q + 1.
 template <int NQ>
-__device__ __forceinline__ void rr_item(const float2* __restrict__ A, float2* __restrict__ C, uint32_t x0,
-                                        float2* s, float scale, unsigned int* st)
+__device__ __forceinline__ void rr_issue(const float2* __restrict__ A, uint32_t x0, float2* s, unsigned int* st)
 {
     using Sh = RrShape<NQ>;
     constexpr int LR = Sh::LR, R = Sh::R;
     constexpr uint64_t kElems = 1ull << (2 * NQ);
     const int t = threadIdx.x;
-    // the piece tile: row r of A, columns ((r ^ x0) & ~(R - 1)) + [0, R), at s[r R]
-    // 4096 value pairs, 16 per thread: pair q is row q >> (lr - 1), columns
-    // ((r ^ x0) & ~(R - 1)) + 2 (q & (R / 2 - 1)) + {0, 1}, tile values 2q, 2q + 1
     const uint32_t sb = (uint32_t)__cvta_generic_to_shared(s);
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
@@ -93,7 +93,33 @@ __device__ __forceinline__ void rr_item(const float2* __restrict__ A, float2* __
         if (in_bounds(st, gi + 1, kElems))
             asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sb + 16u * q), "l"(A + gi) : "memory");
     }
-    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// Hooks of a persistent caller, called by every thread of the CTA at the
+// same point.  `mid` runs after round 1's barrier, when no transform values
+// are held in registers (a caller's bookkeeping there overlaps the other
+// warps' round 2); `hook` runs once the last round has read the shared tile
+// into registers (the rest of the item works from registers and writes C), so
+// that the next item's piece copies, issued there, fly during this item's
+// last transform and stores.  The single-item launch has nothing to do.
+struct RrNoHook {
+    __device__ __forceinline__ void operator()() const {}
+};
+
+// One item.  `issued`: its piece copies were already issued (by the previous
+// item's hook) into s.
+template <int NQ, typename Hook = RrNoHook, typename Mid = RrNoHook>
+__device__ __forceinline__ void rr_item(const float2* __restrict__ A, float2* __restrict__ C, uint32_t x0,
+                                        float2* s, float scale, unsigned int* st, bool issued = false,
+                                        Hook hook = Hook(), Mid mid = Mid())
+{
+    using Sh = RrShape<NQ>;
+    constexpr int LR = Sh::LR, R = Sh::R;
+    constexpr uint64_t kElems = 1ull << (2 * NQ);
+    const int t = threadIdx.x;
+    if (!issued) rr_issue<NQ>(A, x0, s, st);
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
     const uint32_t X0 = x0 >> LR;
     float2 v[32];
@@ -109,6 +135,7 @@ __device__ __forceinline__ void rr_item(const float2* __restrict__ A, float2* __
 #pragma unroll
         for (int w = 0; w < 32; ++w) q[w * Sh::S] = v[w];
         __syncthreads();
+        mid();
         const int warp = t >> 5, w = t & 31;
         const int sg = 2 * (__popc(w & (int)((X0 >> 2) & 31)) & 1);
         // round 2: thread (xl, kh bits 0-1) = warp, w = lane; 2 x 16 values over kh bits 7-10,
@@ -132,6 +159,7 @@ __device__ __forceinline__ void rr_item(const float2* __restrict__ A, float2* __
         const float2* p3 = s + (xl3 * Sh::XS + w * Sh::S + (zk23 << 5));
 #pragma unroll
         for (int j = 0; j < 32; ++j) v[j] = p3[j];
+        hook();
         wht_sub<3, 0, 1>(v);
         wht_sub<3, 8, 1>(v);
         wht_sub<3, 16, 1>(v);
@@ -161,6 +189,7 @@ __device__ __forceinline__ void rr_item(const float2* __restrict__ A, float2* __
         for (int w = 0; w < 32; ++w) q[w * Sh::S] = v[w];
         __syncthreads();
     }
+    mid();
     const int warp = t >> 5, w = t & 31;
     const int sg = 2 * (__popc(w & X0l) & 1);
     if constexpr (NQ == 10) {
@@ -168,6 +197,7 @@ __device__ __forceinline__ void rr_item(const float2* __restrict__ A, float2* __
         const float2* p = s + (warp * Sh::XS + w * Sh::S);
 #pragma unroll
         for (int j = 0; j < 32; ++j) v[j] = p[j];
+        hook();
         wht_sub<5, 0, 1>(v);
         const uint32_t x = x0 + warp;
         float2* row = C + ((uint64_t)x << NQ);
@@ -185,6 +215,7 @@ __device__ __forceinline__ void rr_item(const float2* __restrict__ A, float2* __
 #pragma unroll
             for (int j = 0; j < 16; ++j) v[xh * 16 + j] = p[j];
         }
+        hook();
         wht_sub<4, 0, 1>(v);
         wht_sub<4, 16, 1>(v);
 #pragma unroll
@@ -219,6 +250,7 @@ __device__ __forceinline__ void rr_item(const float2* __restrict__ A, float2* __
         const float2* p = s + (xl * Sh::XS + w * Sh::S + ((warp & 1) << 5));
 #pragma unroll
         for (int j = 0; j < 32; ++j) v[j] = p[j];
+        hook();
 #pragma unroll
         for (int zk = 0; zk < 8; ++zk) {
             // a 4-point transform of registers 4 zk .. 4 zk + 3

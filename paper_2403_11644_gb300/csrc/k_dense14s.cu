@@ -25,7 +25,10 @@
 //
 // Work items are halves (64 KiB each) so that two CTAs share an SM and one
 // CTA's loads overlap the other's arithmetic: a half-tile item covers 64 of
-// the tile's 128 masks, a half-row item 64 of a row's 128 z_lo values.
+// the tile's 128 masks, a half-row item 64 of a row's 128 z_lo values.  An
+// item that has read the shared buffer for the last time issues the next
+// item's A copies into it (if that item is a tile item) before finishing from
+// registers.
 //
 // One persistent kernel runs both passes from an atomic work queue.  The
 // queue order is x-tile major with one tile of look-ahead: round r holds the
@@ -116,6 +119,30 @@ __device__ __forceinline__ void wait_count(const int* p, int target, unsigned lo
 
 } // namespace
 
+// Issues (one commit group, not waited for) the 16-byte copies of half-tile
+// item (xt, cb, h) of the A tile (R = cb ^ xt, cb) into the buffer at buf_a:
+// row rl of the tile contributes columns cl with cl bit 6 = (rl bit 6) ^ h,
+// one contiguous 512-byte run per row.
+template <int LOG>
+__device__ __forceinline__ void issue_half_tile(const float2* __restrict__ A, int xt, int cb, int h, uint32_t buf_a,
+                                                uint64_t pol_a, unsigned int* st)
+{
+    constexpr int kN = 1 << LOG;
+    const int R = cb ^ xt;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const int qc = threadIdx.x + kThreads * i; // 16-byte chunk: row qc >> 5, pair qc & 31
+        const int rl = qc >> 5;
+        const int b = ((rl >> 6) ^ h) & 1;
+        const uint64_t gi = ((uint64_t)(kT * R + rl) << LOG) + (uint64_t)(kT * cb + kH * b) + 2u * (qc & 31);
+        const float2* src = A + (in_bounds(st, gi + 1, (uint64_t)kN * kN) ? gi : 0);
+        asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(buf_a + (uint32_t)qc * 16u),
+                     "l"(src), "l"(pol_a)
+                     : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
 struct StagedTables {
     int* head;  // work-queue counter
     int* done1; // tile items finished per x-tile
@@ -132,7 +159,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     constexpr int kN = G::kN, kTiles = G::kTiles, kPerRound = G::kPerRound, kItems = G::kItems,
                   kSlots = G::kSlots, kZl = G::kZl, kYb = G::kYb, kRb = G::kRb;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ int s_item;
+    __shared__ int s_item, s_next;
     const uint32_t raw_a = su32(smem_raw);
     const uint32_t buf_a = (raw_a + 127u) & ~127u;
     float2* buf = reinterpret_cast<float2*>(smem_raw + (buf_a - raw_a));
@@ -146,6 +173,24 @@ __global__ void __launch_bounds__(kThreads, 2)
     // than the one being processed, so the dependency waits still end)
     int next = 0;
     if (t == 0) next = atomicAdd(tab.head, 1);
+    bool issued = false; // this item's A copies were issued by the previous item
+    // once an item has read the shared buffer for the last time, the next item's
+    // A copies (if it is a tile item) go into it while this item finishes from
+    // registers; every thread calls it at the same point
+    auto prefetch_next = [&]() {
+        if (t == 0) s_next = next;
+        __syncthreads();
+        const int nx = s_next;
+        bool go = false;
+        if (nx < kItems) {
+            const int nr = nx / kPerRound, nj = nx % kPerRound;
+            if (nj < G::kTileItems && nr < kTiles) {
+                issue_half_tile<LOG>(A, nr, nj >> 1, nj & 1, buf_a, pol_a, st);
+                go = true;
+            }
+        }
+        return go;
+    };
     for (;;) {
         if (t == 0) {
             s_item = next;
@@ -163,19 +208,8 @@ __global__ void __launch_bounds__(kThreads, 2)
             // (rl bit 6) ^ h: one contiguous 512-byte run per row.
             const int xt = r, cb = j >> 1, h = j & 1;
             if (xt >= kTiles) { __syncthreads(); continue; }
-            const int R = cb ^ xt;
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const int qc = t + kThreads * i; // 16-byte chunk: row qc >> 5, pair qc & 31
-                const int rl = qc >> 5;
-                const int b = ((rl >> 6) ^ h) & 1;
-                const uint64_t gi = ((uint64_t)(kT * R + rl) << LOG) + (uint64_t)(kT * cb + kH * b) + 2u * (qc & 31);
-                const float2* src = A + (in_bounds(st, gi + 1, (uint64_t)kN * kN) ? gi : 0);
-                asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(buf_a + (uint32_t)qc * 16u),
-                             "l"(src), "l"(pol_a)
-                             : "memory");
-            }
-            asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+            if (!issued) issue_half_tile<LOG>(A, xt, cb, h, buf_a, pol_a, st);
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
             __syncthreads();
             // round a: cl bits 0-4.  Lane l of warp w handles mask xl = 64 h + 32 (w & 1) + l
             // and column group g = w >> 1; at step s it reads cl = 32 g + (s ^ l), so all
@@ -200,16 +234,19 @@ __global__ void __launch_bounds__(kThreads, 2)
             if (t == 0 && xt >= kSlots) wait_count(tab.done2 + (xt - kSlots), G::kRowItems, tab.wait_ns, st);
             __syncthreads();
             float2* stage = tab.stage + ((size_t)(xt % kSlots) * kT + kH * h) * kN;
+            float2 e[8][4];
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int gg = 0; gg < 4; ++gg) e[i][gg] = buf[(8 * warp + i) * kYaStride + 32 * gg + lane];
+            issued = prefetch_next();
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
                 const int row = 8 * warp + i;
-                float2 e[4];
-#pragma unroll
-                for (int gg = 0; gg < 4; ++gg) e[gg] = buf[row * kYaStride + 32 * gg + lane];
-                wht_regs<2>(e);
+                wht_regs<2>(e[i]);
 #pragma unroll
                 for (int gg = 0; gg < 4; ++gg)
-                    __stcg(stage + (size_t)row * kN + kT * cb + 32 * gg + lane, e[gg]);
+                    __stcg(stage + (size_t)row * kN + kT * cb + 32 * gg + lane, e[i][gg]);
             }
             __syncthreads();
             if (t == 0) {
@@ -250,12 +287,16 @@ __global__ void __launch_bounds__(kThreads, 2)
             // round b: cb bits 5 .. LOG-8, then phase, scale and contiguous stores
             constexpr int kPb = kZl / 8; // (c5, z_lo) pairs per thread: 32 kZl / 256
             float2* out = C + (x << LOG) + kZl * h;
+            float2 eb[kPb][1 << kRb];
+#pragma unroll
+            for (int i = 0; i < kPb; ++i)
+#pragma unroll
+                for (int gg = 0; gg < (1 << kRb); ++gg) eb[i][gg] = buf[(32 * gg + kPb * q + i) * kYb + zloc];
+            issued = prefetch_next();
 #pragma unroll
             for (int i = 0; i < kPb; ++i) {
                 const int c5 = kPb * q + i;
-                float2 e[1 << kRb];
-#pragma unroll
-                for (int gg = 0; gg < (1 << kRb); ++gg) e[gg] = buf[(32 * gg + c5) * kYb + zloc];
+                float2 (&e)[1 << kRb] = eb[i];
                 wht_regs<kRb>(e);
 #pragma unroll
                 for (int gg = 0; gg < (1 << kRb); ++gg) {

@@ -57,6 +57,67 @@ __device__ __forceinline__ fx2 csub(fx2 a, fx2 b)
     return a;
 }
 
+// The shared tile as two planes of 16-byte integers (real parts, then
+// imaginary parts) under the padded index of tile_ops.cuh, which keeps warp
+// accesses to 16-byte elements at the minimum number of wavefronts; whole
+// 32-byte values at that index put eight lanes on each bank group.
+struct FxTile {
+    i128* re;
+    i128* im;
+    __device__ __forceinline__ fx2 get(int i) const { return fx2{re[i], im[i]}; }
+    __device__ __forceinline__ void put(int i, const fx2& v) const
+    {
+        re[i] = v.x;
+        im[i] = v.y;
+    }
+};
+
+// The planes of a tile of rows x 2^log_ls values (each plane padded as
+// smem_elems counts it; the launch reserves two planes of 16 bytes).
+__device__ __forceinline__ FxTile fx_tile(void* smem, int rows, int log_ls)
+{
+    const int ls = 1 << log_ls;
+    i128* b = reinterpret_cast<i128*>(smem);
+    return FxTile{b, b + rows * (ls + ls / 16 + 1)};
+}
+
+// Radix-2^NB butterflies over bits [b, b + NB) of the flat tile index.
+template <int NB>
+__device__ __forceinline__ void fx_pass(const FxTile& s, const Smem& sm, int log_e, int b)
+{
+    const int groups = 1 << (log_e - NB);
+    const int lowmask = (1 << b) - 1;
+    for (int q = threadIdx.x; q < groups; q += blockDim.x) {
+        const int base = (q & lowmask) | ((q >> b) << (b + NB));
+        fx2 v[1 << NB];
+#pragma unroll
+        for (int j = 0; j < (1 << NB); ++j) v[j] = s.get(sm.idx(base + (j << b)));
+#pragma unroll
+        for (int h = 1; h < (1 << NB); h <<= 1)
+#pragma unroll
+            for (int i = 0; i < (1 << NB); ++i)
+                if (!(i & h)) {
+                    const fx2 a = v[i], c = v[i + h];
+                    v[i] = cadd(a, c);
+                    v[i + h] = csub(a, c);
+                }
+#pragma unroll
+        for (int j = 0; j < (1 << NB); ++j) s.put(sm.idx(base + (j << b)), v[j]);
+    }
+}
+
+// Flat-index bits [b0, b1) in radix-8 passes, a barrier after each.
+__device__ __forceinline__ void fx_bits(const FxTile& s, const Smem& sm, int log_e, int b0, int b1)
+{
+    for (int b = b0; b < b1; b += 3) {
+        const int nb = min(3, b1 - b);
+        if (nb == 3) fx_pass<3>(s, sm, log_e, b);
+        else if (nb == 2) fx_pass<2>(s, sm, log_e, b);
+        else fx_pass<1>(s, sm, log_e, b);
+        __syncthreads();
+    }
+}
+
 namespace {
 
 template <typename InT> struct in_of;
@@ -147,6 +208,12 @@ __device__ __forceinline__ fx2 times_i_pow(fx2 v, int p)
 
 } // namespace
 
+// Threads per CTA of the tile and strided kernels: two CTAs of 256 threads
+// share an SM (64 KiB tiles, up to 128 registers a thread without spills);
+// two small CTAs wait at their barriers independently, where one CTA of 512
+// threads stalls as a whole.
+constexpr int kFxThreads = 256;
+
 struct FxLaunch {
     const void* src;
     void* dst;
@@ -208,7 +275,7 @@ __global__ void __launch_bounds__(256) k_fx_maxexp(const W* __restrict__ v, uint
 // ------------------------------------------------------------- tile kernel
 
 template <typename InT, Load LD>
-__device__ void fx_load(fx2* s, const Smem& sm, const FxLaunch& p, uint64_t x0, uint64_t k0, int S, unsigned int* st)
+__device__ void fx_load(const FxTile& s, const Smem& sm, const FxLaunch& p, uint64_t x0, uint64_t k0, int S, unsigned int* st)
 {
     const uint64_t N = 1ull << p.n;
     const int log_r = p.log_r, log_l = p.log_l;
@@ -256,13 +323,13 @@ __device__ void fx_load(fx2* s, const Smem& sm, const FxLaunch& p, uint64_t x0, 
                 w = times_i_pow(in_of<InT>::cvt(v[u], S), ph[u]);
             else
                 w = in_of<InT>::cvt(v[u], S);
-            if (d >= 0) s[d] = w;
+            if (d >= 0) s.put(d, w);
         }
     }
 }
 
 template <typename OutT, Store ST>
-__device__ void fx_store(const fx2* s, const Smem& sm, const FxLaunch& p, uint64_t x0, uint64_t k0, int S,
+__device__ void fx_store(const FxTile& s, const Smem& sm, const FxLaunch& p, uint64_t x0, uint64_t k0, int S,
                          unsigned int* st)
 {
     const uint64_t N = 1ull << p.n;
@@ -276,13 +343,13 @@ __device__ void fx_store(const fx2* s, const Smem& sm, const FxLaunch& p, uint64
             const uint64_t r = rb + ((uint64_t)e >> log_r);
             const uint64_t c = ((r ^ x0) & ~(R - 1)) + ((uint64_t)e & (R - 1));
             const uint64_t gi = r * N + c;
-            const fx2 v = s[sm.idx((int)(((r ^ c) - x0) << log_l) + (int)(c - k0))];
+            const fx2 v = s.get(sm.idx((int)(((r ^ c) - x0) << log_l) + (int)(c - k0)));
             if (in_bounds(st, gi, p.dst_elems)) ((OutT*)p.dst)[gi] = out_of<OutT>::cvt(v, 0, o);
         } else {
             const uint64_t x = x0 + (uint64_t)(e >> log_l);
             const uint64_t z = k0 + (uint64_t)(e & ((1 << log_l) - 1));
             const uint64_t gi = (x - p.dst_row0) * N + z;
-            const fx2 v = s[sm.idx(e)];
+            const fx2 v = s.get(sm.idx(e));
             if (!in_bounds(st, gi, p.dst_elems)) continue;
             if constexpr (ST == Store::RowBuf)
                 ((fx2*)p.dst)[gi] = v;
@@ -293,10 +360,10 @@ __device__ void fx_store(const fx2* s, const Smem& sm, const FxLaunch& p, uint64
 }
 
 template <typename InT, typename OutT, Load LD, Store ST>
-__global__ void __launch_bounds__(512) k_fx_tile(FxLaunch p, unsigned int* st)
+__global__ void __launch_bounds__(kFxThreads, 2) k_fx_tile(FxLaunch p, unsigned int* st)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    fx2* s = reinterpret_cast<fx2*>(smem_raw);
+    const FxTile s = fx_tile(smem_raw, 1 << p.log_r, p.log_l);
     const Smem sm = make_smem(p.log_l);
     const int segs_log = p.n - p.log_l;
     const uint64_t blk = (uint64_t)blockIdx.x >> segs_log;
@@ -306,18 +373,18 @@ __global__ void __launch_bounds__(512) k_fx_tile(FxLaunch p, unsigned int* st)
     const int S = fx_shift(p);
     fx_load<InT, LD>(s, sm, p, x0, k0, S, st);
     __syncthreads();
-    wht_bits<3>(s, sm, p.log_r + p.log_l, 0, p.log_l);
+    fx_bits(s, sm, p.log_r + p.log_l, 0, p.log_l);
     fx_store<OutT, ST>(s, sm, p, x0, k0, S, st);
 }
 
 // One CTA per (mask, group of bits >= b1, chunk of 2^log_w low columns) of an
 // intermediate of fixed-point rows; transform over bits [b0, b1).
 template <typename OutT, Store ST>
-__global__ void __launch_bounds__(512) k_fx_strided(FxLaunch p, unsigned int* st)
+__global__ void __launch_bounds__(kFxThreads, 2) k_fx_strided(FxLaunch p, unsigned int* st)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    fx2* s = reinterpret_cast<fx2*>(smem_raw);
     const int nb = p.b1 - p.b0;
+    const FxTile s = fx_tile(smem_raw, 1 << nb, p.log_w);
     const Smem sm = make_smem(p.log_w);
     const uint64_t N = 1ull << p.n;
     const int chunks_log = p.b0 - p.log_w;
@@ -346,16 +413,16 @@ __global__ void __launch_bounds__(512) k_fx_strided(FxLaunch p, unsigned int* st
 #pragma unroll
         for (int u = 0; u < kLoadBatch; ++u) {
             const int e = e0 + u * blockDim.x;
-            if (e < E) s[sm.idx(e)] = v[u];
+            if (e < E) s.put(sm.idx(e), v[u]);
         }
     }
     __syncthreads();
-    wht_bits<3>(s, sm, nb + p.log_w, p.log_w, nb + p.log_w);
+    fx_bits(s, sm, nb + p.log_w, p.log_w, nb + p.log_w);
     const int S = fx_shift(p);
     const FxOut o = fx_out(p, S);
     for (int e = threadIdx.x; e < E; e += blockDim.x) {
         const uint64_t k = kbase + ((uint64_t)(e >> p.log_w) << p.b0) + (uint64_t)(e & wmask);
-        const fx2 v = s[sm.idx(e)];
+        const fx2 v = s.get(sm.idx(e));
         if constexpr (ST == Store::RowPhaseOut) {
             const uint64_t gi = (x - p.dst_row0) * N + k;
             if (in_bounds(st, gi, p.dst_elems))
@@ -367,6 +434,145 @@ __global__ void __launch_bounds__(512) k_fx_strided(FxLaunch p, unsigned int* st
             const uint64_t gi = (k ^ x) * N + k;
             if (in_bounds(st, gi, p.dst_elems)) ((OutT*)p.dst)[gi] = out_of<OutT>::cvt(v, 0, o);
         }
+    }
+}
+
+// ------------------------------------- compile-time shapes (n = 13 .. 15)
+//
+// The multi-pass decompose plans of n = 13, 14, 15 (first pass: 4 masks x
+// 512 values per tile; one strided pass over the remaining n - 9 bits) with
+// every shape a constant: the index arithmetic folds to shifts and masks of
+// 32-bit integers (n <= 15: every element index is below 2^30) and each
+// thread takes a fixed number of values.  Same arithmetic and layout as the
+// generic kernels above.
+
+// Padded tile index of a row length 2^LS (the layout of make_smem).
+template <int LS>
+__device__ __forceinline__ int fx_idx(int f)
+{
+    constexpr int kRs = (1 << LS) + (1 << LS) / 16 + 1;
+    const int col = f & ((1 << LS) - 1);
+    return (f >> LS) * kRs + col + (col >> 4);
+}
+
+// Radix-2^NB butterflies over bits [B, B + NB) of a tile of 2^LOGE values.
+template <int NB, int B, int LOGE, int LS>
+__device__ __forceinline__ void fx_pass_c(const FxTile& s)
+{
+    constexpr int kGroups = 1 << (LOGE - NB);
+    static_assert(kGroups % kFxThreads == 0, "whole groups per thread");
+#pragma unroll 1
+    for (int q = threadIdx.x; q < kGroups; q += kFxThreads) {
+        const int base = (q & ((1 << B) - 1)) | ((q >> B) << (B + NB));
+        fx2 v[1 << NB];
+#pragma unroll
+        for (int j = 0; j < (1 << NB); ++j) v[j] = s.get(fx_idx<LS>(base + (j << B)));
+#pragma unroll
+        for (int h = 1; h < (1 << NB); h <<= 1)
+#pragma unroll
+            for (int i = 0; i < (1 << NB); ++i)
+                if (!(i & h)) {
+                    const fx2 a = v[i], c = v[i + h];
+                    v[i] = cadd(a, c);
+                    v[i + h] = csub(a, c);
+                }
+#pragma unroll
+        for (int j = 0; j < (1 << NB); ++j) s.put(fx_idx<LS>(base + (j << B)), v[j]);
+    }
+}
+
+// Bits [B0, B1) in radix-8 passes (the last one narrower), a barrier after each.
+template <int B0, int B1, int LOGE, int LS>
+__device__ __forceinline__ void fx_bits_c(const FxTile& s)
+{
+    if constexpr (B0 < B1) {
+        constexpr int NB = B1 - B0 < 3 ? B1 - B0 : 3;
+        fx_pass_c<NB, B0, LOGE, LS>(s);
+        __syncthreads();
+        fx_bits_c<B0 + NB, B1, LOGE, LS>(s);
+    }
+}
+
+// First pass of a chunk: 2^LR masks x 2^LL values gathered from A (row view,
+// as load_gather), transformed over the LL low bits, stored as fixed-point
+// rows of the intermediate.
+template <typename InT, int LR, int LL>
+__global__ void __launch_bounds__(kFxThreads, 2) k_fx_tile_c(FxLaunch p, unsigned int* st)
+{
+    constexpr int kE = 1 << (LR + LL), kPer = kE / kFxThreads, kR = 1 << LR, kL = 1 << LL;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const FxTile s = fx_tile(smem_raw, kR, LL);
+    const int n = p.n, t = threadIdx.x;
+    const int segs_log = n - LL;
+    const uint32_t blk = blockIdx.x >> segs_log, seg = blockIdx.x & ((1u << segs_log) - 1);
+    const uint32_t x0 = (uint32_t)p.x_begin + (blk << LR), k0 = seg << LL;
+    const uint32_t rb = (k0 ^ x0) & ~(uint32_t)(kL - 1);
+    const int S = fx_shift(p);
+    const InT* A = (const InT*)p.src;
+    InT v[kPer];
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+        // row r of A supplies the aligned block of 2^LR columns r ^ x
+        const int e = t + u * kFxThreads;
+        const uint32_t r = rb + (uint32_t)(e >> LR);
+        const uint32_t c = ((r ^ x0) & ~(uint32_t)(kR - 1)) + (uint32_t)(e & (kR - 1));
+        const uint32_t gi = (r << n) + c;
+        v[u] = __ldg(A + (in_bounds(st, gi, p.src_elems) ? gi : 0));
+    }
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+        const int e = t + u * kFxThreads;
+        const uint32_t r = rb + (uint32_t)(e >> LR);
+        const uint32_t c = ((r ^ x0) & ~(uint32_t)(kR - 1)) + (uint32_t)(e & (kR - 1));
+        s.put(fx_idx<LL>((int)(((r ^ c) - x0) << LL) + (int)(c - k0)), in_of<InT>::cvt(v[u], S));
+    }
+    __syncthreads();
+    fx_bits_c<0, LL, LR + LL, LL>(s);
+    fx2* dst = (fx2*)p.dst;
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+        const int e = t + u * kFxThreads;
+        const uint32_t x = x0 + (uint32_t)(e >> LL), z = k0 + (uint32_t)(e & (kL - 1));
+        const uint32_t gi = ((x - (uint32_t)p.dst_row0) << n) + z;
+        if (in_bounds(st, gi, p.dst_elems)) dst[gi] = s.get(fx_idx<LL>(e));
+    }
+}
+
+// The strided pass that finishes a chunk: per mask and chunk of 2^LW low
+// columns, bits [b0, b0 + NB) = [n - NB, n), then the phase, the scale and the
+// rounding to the output type.
+template <typename OutT, int NB, int LW>
+__global__ void __launch_bounds__(kFxThreads, 2) k_fx_strided_c(FxLaunch p, unsigned int* st)
+{
+    constexpr int kE = 1 << (NB + LW), kPer = kE / kFxThreads, kW = 1 << LW;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const FxTile s = fx_tile(smem_raw, 1 << NB, LW);
+    const int n = p.n, b0 = n - NB, t = threadIdx.x;
+    const int chunks_log = b0 - LW;
+    const uint32_t chunk = blockIdx.x & ((1u << chunks_log) - 1);
+    const uint32_t x = (uint32_t)p.x_begin + (blockIdx.x >> chunks_log);
+    const uint32_t kbase = chunk << LW;
+    const fx2* src = (const fx2*)p.src + ((size_t)(x - (uint32_t)p.src_row0) << n);
+    fx2 v[kPer];
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+        const int e = t + u * kFxThreads;
+        const uint32_t k = kbase + ((uint32_t)(e >> LW) << b0) + (uint32_t)(e & (kW - 1));
+        v[u] = src[in_bounds(st, ((uint64_t)(x - (uint32_t)p.src_row0) << n) + k, p.src_elems) ? k : 0];
+    }
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) s.put(fx_idx<LW>(t + u * kFxThreads), v[u]);
+    __syncthreads();
+    fx_bits_c<LW, LW + NB, NB + LW, LW>(s);
+    const int S = fx_shift(p);
+    const FxOut o = fx_out(p, S);
+    OutT* dst = (OutT*)p.dst;
+#pragma unroll 2
+    for (int u = 0; u < kPer; ++u) {
+        const int e = t + u * kFxThreads;
+        const uint32_t k = kbase + ((uint32_t)(e >> LW) << b0) + (uint32_t)(e & (kW - 1));
+        const uint32_t gi = ((x - (uint32_t)p.dst_row0) << n) + k;
+        if (in_bounds(st, gi, p.dst_elems)) dst[gi] = out_of<OutT>::cvt(s.get(fx_idx<LW>(e)), __popc(x & k) & 3, o);
     }
 }
 
@@ -387,7 +593,7 @@ cudaError_t run_fx_tile(const FxLaunch& p, unsigned int* st, cudaStream_t s)
     cudaError_t e = fx_smem(kern, bytes);
     if (e != cudaSuccess) return e;
     const uint64_t blocks = (p.x_count >> p.log_r) << (p.n - p.log_l);
-    kern<<<(unsigned)blocks, 512, bytes, s>>>(p, st);
+    kern<<<(unsigned)blocks, kFxThreads, bytes, s>>>(p, st);
     return cudaGetLastError();
 }
 
@@ -399,7 +605,7 @@ cudaError_t run_fx_strided(const FxLaunch& p, unsigned int* st, cudaStream_t s)
     cudaError_t e = fx_smem(kern, bytes);
     if (e != cudaSuccess) return e;
     const uint64_t blocks = p.x_count << ((p.n - p.b1) + (p.b0 - p.log_w));
-    kern<<<(unsigned)blocks, 512, bytes, s>>>(p, st);
+    kern<<<(unsigned)blocks, kFxThreads, bytes, s>>>(p, st);
     return cudaGetLastError();
 }
 
@@ -449,6 +655,74 @@ cudaError_t fx_strided_types(const FxLaunch& p, ptdr_dtype out_t, unsigned int* 
         break;
     }
     return cudaErrorInvalidValue;
+}
+
+template <typename InT>
+cudaError_t run_fx_tile_c(const FxLaunch& p, unsigned int* st, cudaStream_t s)
+{
+    auto kern = k_fx_tile_c<InT, 2, 9>;
+    const size_t bytes = smem_elems(4, 9) * sizeof(fx2);
+    cudaError_t e = fx_smem(kern, bytes);
+    if (e != cudaSuccess) return e;
+    const uint64_t blocks = (p.x_count >> 2) << (p.n - 9);
+    kern<<<(unsigned)blocks, kFxThreads, bytes, s>>>(p, st);
+    return cudaGetLastError();
+}
+
+template <typename OutT, int NB, int LW>
+cudaError_t run_fx_strided_c(const FxLaunch& p, unsigned int* st, cudaStream_t s)
+{
+    auto kern = k_fx_strided_c<OutT, NB, LW>;
+    const size_t bytes = smem_elems((size_t)1 << NB, LW) * sizeof(fx2);
+    cudaError_t e = fx_smem(kern, bytes);
+    if (e != cudaSuccess) return e;
+    const uint64_t blocks = p.x_count << (p.n - NB - LW);
+    kern<<<(unsigned)blocks, kFxThreads, bytes, s>>>(p, st);
+    return cudaGetLastError();
+}
+
+template <typename OutT>
+cudaError_t fx_strided_c_shape(const FxLaunch& p, unsigned int* st, cudaStream_t s)
+{
+    const int nb = p.b1 - p.b0;
+    if (nb == 4 && p.log_w == 7) return run_fx_strided_c<OutT, 4, 7>(p, st, s);
+    if (nb == 5 && p.log_w == 6) return run_fx_strided_c<OutT, 5, 6>(p, st, s);
+    if (nb == 6 && p.log_w == 5) return run_fx_strided_c<OutT, 6, 5>(p, st, s);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t fx_strided_c_types(const FxLaunch& p, ptdr_dtype out_t, unsigned int* st, cudaStream_t s)
+{
+    switch (out_t) {
+    case PTDR_C64: return fx_strided_c_shape<float2>(p, st, s);
+    case PTDR_C128: return fx_strided_c_shape<double2>(p, st, s);
+    case PTDR_F32: return fx_strided_c_shape<float>(p, st, s);
+    case PTDR_F64: return fx_strided_c_shape<double>(p, st, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t fx_tile_c_types(const FxLaunch& p, ptdr_dtype in_t, unsigned int* st, cudaStream_t s)
+{
+    switch (in_t) {
+    case PTDR_C64: return run_fx_tile_c<float2>(p, st, s);
+    case PTDR_C128: return run_fx_tile_c<double2>(p, st, s);
+    case PTDR_F32: return run_fx_tile_c<float>(p, st, s);
+    case PTDR_F64: return run_fx_tile_c<double>(p, st, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// The decompose plans the compile-time kernels cover: 4 masks x 512 values
+// in the first pass, then one strided pass over the remaining bits with the
+// (bits, columns) shapes of n = 13, 14, 15.
+bool fx_shapes_c(const DensePlan& plan)
+{
+    if (plan.compose || plan.single || plan.log_r != 2 || plan.log_l != 9 || plan.passes.size() != 1) return false;
+    const StridedPass& q = plan.passes[0];
+    const int nb = q.b1 - q.b0;
+    return q.b0 == 9 && q.b1 == plan.n &&
+           ((nb == 4 && q.log_w == 7) || (nb == 5 && q.log_w == 6) || (nb == 6 && q.log_w == 5));
 }
 
 } // namespace
@@ -525,7 +799,9 @@ cudaError_t launch_fixed(const DensePlan& plan, const void* in, void* out, void*
         t.src_row0 = 0;
         t.src_elems = N * N;
         t.dst_elems = plan.chunk * N;
+        const bool shaped = fx_shapes_c(plan);
         e = plan.compose ? fx_tile_types<Load::RowPhaseC, Store::RowBuf>(t, plan.in_t, plan.out_t, st, s)
+            : shaped     ? fx_tile_c_types(t, plan.in_t, st, s)
                          : fx_tile_types<Load::GatherA, Store::RowBuf>(t, plan.in_t, plan.out_t, st, s);
         for (size_t i = 0; i < plan.passes.size() && e == cudaSuccess; ++i) {
             const bool last = i + 1 == plan.passes.size();
@@ -548,6 +824,7 @@ cudaError_t launch_fixed(const DensePlan& plan, const void* in, void* out, void*
                 q.dst_row0 = 0;
                 q.dst_elems = N * N;
                 e = plan.compose ? fx_strided_types<Store::ScatterA>(q, plan.out_t, st, s)
+                    : shaped     ? fx_strided_c_types(q, plan.out_t, st, s)
                                  : fx_strided_types<Store::RowPhaseOut>(q, plan.out_t, st, s);
             }
         }

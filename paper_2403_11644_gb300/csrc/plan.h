@@ -16,7 +16,7 @@ constexpr size_t kRowTileBytes = 128 * 1024;
 // Workspace cap for the intermediate of chunked multi-pass launches.
 constexpr size_t kChunkBytes = 256ull << 20;
 // Intermediate of the fixed-point path per chunk of masks: small enough to stay in L2.
-constexpr size_t kFixedChunkBytes = 64ull << 20;
+constexpr size_t kFixedChunkBytes = 128ull << 20;
 
 struct StridedPass {
     int b0, b1, log_w;

@@ -105,8 +105,8 @@ def test_workspace_sizes(lib):
     # 32-byte intermediate rows once a row no longer fits one tile (n >= 13)
     assert ws_size(lib, 0, 12, C64, C128, _lib.PREC_FIXED_I128) == (OK, 256)
     assert ws_size(lib, 1, 10, C128, C128, _lib.PREC_FIXED_I128) == (OK, 256)
-    assert ws_size(lib, 0, 14, C64, C128, _lib.PREC_FIXED_I128) == (OK, 256 + (64 << 20))
-    assert ws_size(lib, 1, 15, C128, C64, _lib.PREC_FIXED_I128) == (OK, 256 + (64 << 20))
+    assert ws_size(lib, 0, 14, C64, C128, _lib.PREC_FIXED_I128) == (OK, 256 + (128 << 20))
+    assert ws_size(lib, 1, 15, C128, C64, _lib.PREC_FIXED_I128) == (OK, 256 + (128 << 20))
     st, b = ws_size(lib, 1, 15, C64, C64, _lib.PREC_FP32)  # compose multi-pass
     assert st == OK and b > 0
     assert ws_size(lib, 0, 0, C64, C64, _lib.PREC_FP32)[0] == INVALID

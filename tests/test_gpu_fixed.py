@@ -62,6 +62,39 @@ def test_fixed_workload_n14():
     assert ptdr.last_device_status() == 0
 
 
+def test_fixed_workload_n15_sampled():
+    """dense n = 15 complex64 (first pass + one strided pass over six bits) into
+    complex64: sampled rows at half an ulp of float32, against the FWHT check."""
+    A = workloads.dense_c64_direct(15, 1515)
+    C = ptdr.decompose(dev(A), precision="fixed", out_dtype=torch.complex64)
+    xs = workloads.sample_masks(15, 1515, count=6)
+    got = host(C[torch.from_numpy(xs.astype(np.int64)).cuda()])
+    err = rel_err(got, oracle.fwht(A, xs=xs))
+    print(f"fixed n=15 complex64 -> complex64 (sampled): rel err {err:.3e}")
+    assert err <= 2.0 ** -24 * (1 + 1e-6)
+    assert ptdr.last_device_status() == 0
+
+
+@pytest.mark.parametrize("out_dtype", [torch.float64, torch.float32, torch.complex64])
+def test_fixed_n13_hermitian_output_types(out_dtype):
+    """n = 13 Hermitian complex128 (first pass + one strided pass over four bits):
+    real outputs hold the whole (real, Thm 2) coefficient, complex64 the rounded one."""
+    A = workloads.dense(13, 1313, hermitian=True)
+    C = host(ptdr.decompose(dev(A), precision="fixed", out_dtype=out_dtype))
+    ref = oracle.fwht(A)
+    bound = TOL["fixed"] if out_dtype == torch.float64 else 2.0 ** -24 * (1 + 1e-6)
+    assert rel_err(C, ref.real if out_dtype.is_floating_point else ref) <= bound
+    assert ptdr.last_device_status() == 0
+
+
+def test_fixed_n13_real_float32_input():
+    """A real float32 matrix of n = 13 (the imaginary parts enter as zeros)."""
+    A = np.ascontiguousarray(workloads.dense(13, 1314).real.astype(np.float32))
+    C = host(ptdr.decompose(dev(A), precision="fixed", out_dtype=torch.complex128))
+    assert rel_err(C, oracle.fwht(A.astype(np.complex128))) <= TOL["fixed"]
+    assert ptdr.last_device_status() == 0
+
+
 def test_fixed_complex64_output_rounded_once():
     """complex64 output: each coefficient is the exact sum rounded once, so the error is
     at most half an ulp of float32 (2^-24 of the largest coefficient)."""

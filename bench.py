@@ -34,14 +34,14 @@ METRIC = "Pauli coeffs/s and HBM GB/s at n=14, split-BF16 TC vs FP64 plain"
 # path, from one ncu capture each (summaries under profiles/).  A figure is
 # reported only while the sources it was taken from are unchanged.
 NCU_TRAFFIC = {
-    "fp32": {"kernel": "k_dense_staged", "bytes": 2_158_049_280 + 2_157_005_824,
+    "fp32": {"kernel": "k_dense_staged", "bytes": 2_147_567_616 + 2_126_268_416,
              "sources": {"paper_2403_11644_gb300/csrc/k_dense14s.cu":
-                         "f594787dd5a28f96f4936cba21eb9c3ce66a261f694b1cd2e89fbdf8b9658b1b",
+                         "445137d630a6dfdc430e2afe11cbfdf231c3599826ece125e76d65f387db1ec5",
                          "paper_2403_11644_gb300/csrc/common.cuh":
                          "0b8af7566a7fe16e8503406413c2ad8e3700521db352a206df357200a0645186"}},
-    "bf16x3": {"kernel": "k_tc14_pipe", "bytes": 2_148_109_056 + 2_117_101_056,
+    "bf16x3": {"kernel": "k_tc14_pipe", "bytes": 2_148_103_168 + 2_117_208_064,
                "sources": {"paper_2403_11644_gb300/csrc/k_tc14p.cu":
-                           "73bfacd58afdf0c55982c9debede00e63df09eac46fdfd6995f02a1cfad12e0e",
+                           "fac413e7ad250256122c5ce63f7bfeb02adc1343dabc06324a7e9732336c9481",
                            "paper_2403_11644_gb300/csrc/common.cuh":
                            "0b8af7566a7fe16e8503406413c2ad8e3700521db352a206df357200a0645186"}},
 }
@@ -527,7 +527,7 @@ def main():
     global N_QUBITS
     N_QUBITS = args.n
     prec = args.precision or "bf16x3"
-    out_dtype = torch.complex128 if prec == "fp64" else torch.complex64
+    out_dtype = torch.complex128 if prec in ("fp64", "fixed") else torch.complex64
     A_h = workloads.dense_c64_direct(N_QUBITS, (SEED if N_QUBITS == 14 else N_QUBITS) + rank)
     A = torch.from_numpy(A_h).to(dev)
     C = torch.empty((1 << N_QUBITS, 1 << N_QUBITS), dtype=out_dtype, device=dev)

@@ -90,8 +90,8 @@ constexpr int kGroupsPerWarp = 32 / kLoadWarps; // tile jobs: groups of 4 comple
 constexpr int kUnitsPerWarp = 16 / kLoadWarps;  // row jobs: units of 8 zl per loader thread and chunk
 constexpr int kEpiWarps = 8;
 constexpr int kMmaWarp = kLoadWarps + kEpiWarps; // 24
-constexpr int kProdWarp = kMmaWarp + 1;          // 17
-constexpr int kPubWarp = kProdWarp + 1;          // 18
+constexpr int kProdWarp = kMmaWarp + 1;          // 25
+constexpr int kPubWarp = kProdWarp + 1;          // 26
 constexpr int kThreads = (kPubWarp + 1) * 32;    // 864
 constexpr int kChunks = 4;                        // K chunks of 32 rows per job
 constexpr uint32_t kSplitBytes = 32u * 256u * 2u; // one split of a chunk: 32 K x 256 M/N bf16

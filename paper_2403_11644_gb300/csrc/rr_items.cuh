@@ -70,7 +70,7 @@ __device__ __forceinline__ void rr_put(float2* C, uint32_t x, uint32_t z, int sg
 {
     const float2 pa = phase_neg_i(a, __popc(x & z) + sg, scale);
     const float2 pb = phase_neg_i(b, __popc(x & (z + 1)) + sg, scale);
-    *reinterpret_cast<float4*>(C + z) = make_float4(pa.x, pa.y, pb.x, pb.y);
+    __stcs(reinterpret_cast<float4*>(C + z), make_float4(pa.x, pa.y, pb.x, pb.y));
 }
 
 // Issues (one commit group, not waited for) the 16-byte copies of item x0's

@@ -27,6 +27,7 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "pair_ops.cuh"
 #include "plan.h"
 
 namespace ptdr {
@@ -55,11 +56,7 @@ __device__ __forceinline__ void wht_regs(float2 (&v)[1 << NB])
     for (int h = 1; h < (1 << NB); h <<= 1)
 #pragma unroll
         for (int i = 0; i < (1 << NB); ++i)
-            if (!(i & h)) {
-                float2 a = v[i], b = v[i + h];
-                v[i] = make_float2(a.x + b.x, a.y + b.y);
-                v[i + h] = make_float2(a.x - b.x, a.y - b.y);
-            }
+            if (!(i & h)) bfly2(v[i], v[i + h]);
 }
 
 __device__ __forceinline__ int ld_acquire(const int* p)

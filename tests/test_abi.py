@@ -94,7 +94,7 @@ def test_workspace_sizes(lib):
     assert ws_size(lib, 0, 14, C128, C64, _lib.PREC_FP32) == (OK, 0)
     assert ws_size(lib, 0, 12, C64, C64, _lib.PREC_SPLIT_BF16_TC)[0] == UNSUPPORTED
     assert ws_size(lib, 0, 14, C64, C64, 4)[0] == INVALID  # no precision 4
-    # n = 15 complex64: the staged kernel's two 32 MiB staging slots (the generic
+    # n = 15 complex64: the staged kernel's three 32 MiB staging slots (the generic
     # multi-pass plan, taken for unaligned buffers, keeps its intermediate in C)
     assert ws_size(lib, 0, 15, C64, C64, _lib.PREC_FP32) == (OK, 4096 + (96 << 20))
     assert ws_size(lib, 0, 15, C128, C64, _lib.PREC_FP32) == (OK, 0)

@@ -25,49 +25,96 @@ __host__ __device__ __forceinline__ int batch_log_r(int n, int tile_log)
     return lr;
 }
 
-// Planner: counting sort of the matrices by descending n, and the first work
-// item of each.  One thread; the table is a few entries per matrix.
-__global__ void k_batch_plan(const int* d_n, int count, BatchTables tab, int tile_log,
-                             unsigned int* st)
+// Planner: stable counting sort of the matrices by descending n, and the
+// first work item of each rank.  One CTA of kPlanThreads threads:
+//   1. a class histogram of the sizes (shared atomics);
+//   2. per class (largest n first) its first rank and its first work item:
+//      every matrix of size n has the same number of items, so the first item
+//      of rank k in class n is that class's first item plus (k - pos[n])
+//      times the class's items per matrix -- no sequential scan;
+//   3. the ranks, chunk by chunk in index order: a matrix's rank is its class's
+//      first rank, plus the matrices of its class in earlier chunks, plus those
+//      in earlier warps of the chunk (per-warp class counts), plus those in
+//      earlier lanes of its warp (__match_any_sync), so the order inside a
+//      class is the index order.
+constexpr int kPlanThreads = 1024;
+constexpr int kPlanWarps = kPlanThreads / 32;
+constexpr int kClasses = kBatchMaxN + 1; // n = 1 .. kBatchMaxN (entry 0 unused)
+
+__global__ void __launch_bounds__(kPlanThreads) k_batch_plan(const int* d_n, int count, BatchTables tab, int tile_log,
+                                                             unsigned int* st)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    int cls[kBatchMaxN + 2];
-    for (int i = 0; i <= kBatchMaxN + 1; ++i) cls[i] = 0;
-    bool bad = false;
-    for (int i = 0; i < count; ++i) {
+    __shared__ int s_cls[kClasses], s_pos[kClasses], s_run[kClasses], s_chunk[kClasses], s_wcnt[kPlanWarps][kClasses];
+    __shared__ long long s_base[kClasses];
+    __shared__ int s_bad, s_ranked;
+    __shared__ long long s_items;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    if (t < kClasses) {
+        s_cls[t] = 0;
+        s_run[t] = 0;
+    }
+    if (t == 0) s_bad = 0;
+    __syncthreads();
+    for (int i = t; i < count; i += kPlanThreads) {
         const int n = d_n[i];
-        if (n < 1 || n > kBatchMaxN) {
-            bad = true;
-            continue;
+        if (n < 1 || n > kBatchMaxN) s_bad = 1;
+        else atomicAdd(&s_cls[n], 1);
+    }
+    __syncthreads();
+    if (t == 0) {
+        int r = 0;
+        long long items = 0;
+        for (int n = kBatchMaxN; n >= 1; --n) {
+            s_pos[n] = r;
+            s_base[n] = items;
+            r += s_cls[n];
+            items += (long long)s_cls[n] << (n - batch_log_r(n, tile_log));
         }
-        ++cls[n];
+        s_ranked = r;
+        s_items = items;
+        if (s_bad || items > tab.max_items) {
+            report_status(st, PTDR_ERR_INVALID_ARG);
+            s_ranked = 0;
+            s_items = 0;
+        }
+        tab.hdr[0] = 0;                 // queue head
+        tab.hdr[1] = (int)s_items;      // total items
+        tab.hdr[2] = s_ranked;          // ranked matrices
     }
-    // class start ranks, largest n first
-    int pos[kBatchMaxN + 2];
-    int r = 0;
-    for (int n = kBatchMaxN; n >= 1; --n) {
-        pos[n] = r;
-        r += cls[n];
+    __syncthreads();
+    if (s_ranked == 0) return;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int c0 = 0; c0 < count; c0 += kPlanThreads) {
+        const int i = c0 + t;
+        const int n = i < count ? d_n[i] : 0; // 0: no matrix (sizes are valid here)
+        const unsigned same = __match_any_sync(0xffffffffu, n);
+        const int before = __popc(same & lt);
+        for (int k = t; k < kPlanWarps * kClasses; k += kPlanThreads) s_wcnt[k / kClasses][k % kClasses] = 0;
+        __syncthreads();
+        if (n > 0 && before == 0) s_wcnt[warp][n] = __popc(same);
+        __syncthreads();
+        // exclusive prefix over the warps, per class; the chunk's totals go to s_run
+        if (t < kClasses && t > 0) {
+            int acc = 0;
+            for (int w = 0; w < kPlanWarps; ++w) {
+                const int v = s_wcnt[w][t];
+                s_wcnt[w][t] = acc;
+                acc += v;
+            }
+            s_chunk[t] = acc;
+        }
+        __syncthreads();
+        if (n > 0) tab.order[s_pos[n] + s_run[n] + s_wcnt[warp][n] + before] = i;
+        __syncthreads();
+        if (t < kClasses && t > 0) s_run[t] += s_chunk[t];
+        __syncthreads();
     }
-    for (int i = 0; i < count; ++i) {
-        const int n = d_n[i];
-        if (n < 1 || n > kBatchMaxN) continue;
-        tab.order[pos[n]++] = i;
+    // first work item of every rank
+    for (int k = t; k < s_ranked; k += kPlanThreads) {
+        int n = kBatchMaxN;
+        while (n > 1 && k >= s_pos[n] + s_run[n]) --n; // s_run[n] = class size by now
+        tab.start[k] = (int)(s_base[n] + ((long long)(k - s_pos[n]) << (n - batch_log_r(n, tile_log))));
     }
-    long long items = 0;
-    for (int k = 0; k < r; ++k) {
-        const int n = d_n[tab.order[k]];
-        tab.start[k] = (int)items;
-        items += 1ll << (n - batch_log_r(n, tile_log));
-    }
-    if (bad || items > tab.max_items) {
-        report_status(st, PTDR_ERR_INVALID_ARG);
-        items = 0;
-        r = 0;
-    }
-    tab.hdr[0] = 0;            // queue head
-    tab.hdr[1] = (int)items;   // total items
-    tab.hdr[2] = r;            // ranked matrices
 }
 
 // One work item as the loop needs it: its queue index (>= total: no item),
@@ -265,7 +312,7 @@ static cudaError_t run_batched(const BatchLaunch& p, const BatchTables& tab, uns
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, need)) != cudaSuccess)
         return e;
     const int grid = sms * (per_sm > 0 ? per_sm : 1);
-    k_batch_plan<<<1, 32, 0, s>>>(p.d_n, p.count, tab, p.tile_log, st);
+    k_batch_plan<<<1, kPlanThreads, 0, s>>>(p.d_n, p.count, tab, p.tile_log, st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     kern<<<grid, 256, need, s>>>(p, tab, st);
     return cudaGetLastError();

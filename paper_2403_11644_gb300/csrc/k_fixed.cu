@@ -446,17 +446,29 @@ __global__ void __launch_bounds__(kFxThreads, 2) k_fx_strided(FxLaunch p, unsign
 // thread takes a fixed number of values.  Same arithmetic and layout as the
 // generic kernels above.
 
-// Padded tile index of a row length 2^LS (the layout of make_smem).
+// Tile layouts: the padded index of a row length 2^LS with one pad value
+// every 2^PS values and row stride RS.  FxLay<LS> is the layout of make_smem
+// (a pad every 16, stride 2^LS + 2^LS/16 + 1).  FxLayGather is the first-pass
+// tile of 4 rows x 512: a pad every 8 and stride 580 put every warp access of
+// that kernel -- the gather's stores to four XOR-permuted rows, the radix-8
+// passes, the row reads -- at the minimum of four wavefronts of 16-byte
+// elements (checked on a model of all its access patterns), where the
+// make_smem layout took 12 for the gather and 8 for the first pass.
+template <int LS, int PS, int RS>
+struct FxLayout {
+    static constexpr int kRs = RS;
+    __device__ static __forceinline__ int idx(int f)
+    {
+        const int col = f & ((1 << LS) - 1);
+        return (f >> LS) * RS + col + (col >> PS);
+    }
+};
 template <int LS>
-__device__ __forceinline__ int fx_idx(int f)
-{
-    constexpr int kRs = (1 << LS) + (1 << LS) / 16 + 1;
-    const int col = f & ((1 << LS) - 1);
-    return (f >> LS) * kRs + col + (col >> 4);
-}
+using FxLay = FxLayout<LS, 4, (1 << LS) + (1 << LS) / 16 + 1>;
+using FxLayGather = FxLayout<9, 3, 580>;
 
 // Radix-2^NB butterflies over bits [B, B + NB) of a tile of 2^LOGE values.
-template <int NB, int B, int LOGE, int LS>
+template <int NB, int B, int LOGE, typename Lay>
 __device__ __forceinline__ void fx_pass_c(const FxTile& s)
 {
     constexpr int kGroups = 1 << (LOGE - NB);
@@ -466,7 +478,7 @@ __device__ __forceinline__ void fx_pass_c(const FxTile& s)
         const int base = (q & ((1 << B) - 1)) | ((q >> B) << (B + NB));
         fx2 v[1 << NB];
 #pragma unroll
-        for (int j = 0; j < (1 << NB); ++j) v[j] = s.get(fx_idx<LS>(base + (j << B)));
+        for (int j = 0; j < (1 << NB); ++j) v[j] = s.get(Lay::idx(base + (j << B)));
 #pragma unroll
         for (int h = 1; h < (1 << NB); h <<= 1)
 #pragma unroll
@@ -477,19 +489,19 @@ __device__ __forceinline__ void fx_pass_c(const FxTile& s)
                     v[i + h] = csub(a, c);
                 }
 #pragma unroll
-        for (int j = 0; j < (1 << NB); ++j) s.put(fx_idx<LS>(base + (j << B)), v[j]);
+        for (int j = 0; j < (1 << NB); ++j) s.put(Lay::idx(base + (j << B)), v[j]);
     }
 }
 
 // Bits [B0, B1) in radix-8 passes (the last one narrower), a barrier after each.
-template <int B0, int B1, int LOGE, int LS>
+template <int B0, int B1, int LOGE, typename Lay>
 __device__ __forceinline__ void fx_bits_c(const FxTile& s)
 {
     if constexpr (B0 < B1) {
         constexpr int NB = B1 - B0 < 3 ? B1 - B0 : 3;
-        fx_pass_c<NB, B0, LOGE, LS>(s);
+        fx_pass_c<NB, B0, LOGE, Lay>(s);
         __syncthreads();
-        fx_bits_c<B0 + NB, B1, LOGE, LS>(s);
+        fx_bits_c<B0 + NB, B1, LOGE, Lay>(s);
     }
 }
 
@@ -500,8 +512,11 @@ template <typename InT, int LR, int LL>
 __global__ void __launch_bounds__(kFxThreads, 2) k_fx_tile_c(FxLaunch p, unsigned int* st)
 {
     constexpr int kE = 1 << (LR + LL), kPer = kE / kFxThreads, kR = 1 << LR, kL = 1 << LL;
+    static_assert(LR == 2 && LL == 9, "the gather layout is laid out for 4 x 512 tiles");
+    using Lay = FxLayGather;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const FxTile s = fx_tile(smem_raw, kR, LL);
+    i128* const plane = reinterpret_cast<i128*>(smem_raw);
+    const FxTile s{plane, plane + kR * Lay::kRs};
     const int n = p.n, t = threadIdx.x;
     const int segs_log = n - LL;
     const uint32_t blk = blockIdx.x >> segs_log, seg = blockIdx.x & ((1u << segs_log) - 1);
@@ -524,17 +539,17 @@ __global__ void __launch_bounds__(kFxThreads, 2) k_fx_tile_c(FxLaunch p, unsigne
         const int e = t + u * kFxThreads;
         const uint32_t r = rb + (uint32_t)(e >> LR);
         const uint32_t c = ((r ^ x0) & ~(uint32_t)(kR - 1)) + (uint32_t)(e & (kR - 1));
-        s.put(fx_idx<LL>((int)(((r ^ c) - x0) << LL) + (int)(c - k0)), in_of<InT>::cvt(v[u], S));
+        s.put(Lay::idx((int)(((r ^ c) - x0) << LL) + (int)(c - k0)), in_of<InT>::cvt(v[u], S));
     }
     __syncthreads();
-    fx_bits_c<0, LL, LR + LL, LL>(s);
+    fx_bits_c<0, LL, LR + LL, Lay>(s);
     fx2* dst = (fx2*)p.dst;
 #pragma unroll
     for (int u = 0; u < kPer; ++u) {
         const int e = t + u * kFxThreads;
         const uint32_t x = x0 + (uint32_t)(e >> LL), z = k0 + (uint32_t)(e & (kL - 1));
         const uint32_t gi = ((x - (uint32_t)p.dst_row0) << n) + z;
-        if (in_bounds(st, gi, p.dst_elems)) dst[gi] = s.get(fx_idx<LL>(e));
+        if (in_bounds(st, gi, p.dst_elems)) dst[gi] = s.get(Lay::idx(e));
     }
 }
 
@@ -561,9 +576,9 @@ __global__ void __launch_bounds__(kFxThreads, 2) k_fx_strided_c(FxLaunch p, unsi
         v[u] = src[in_bounds(st, ((uint64_t)(x - (uint32_t)p.src_row0) << n) + k, p.src_elems) ? k : 0];
     }
 #pragma unroll
-    for (int u = 0; u < kPer; ++u) s.put(fx_idx<LW>(t + u * kFxThreads), v[u]);
+    for (int u = 0; u < kPer; ++u) s.put(FxLay<LW>::idx(t + u * kFxThreads), v[u]);
     __syncthreads();
-    fx_bits_c<LW, LW + NB, NB + LW, LW>(s);
+    fx_bits_c<LW, LW + NB, NB + LW, FxLay<LW>>(s);
     const int S = fx_shift(p);
     const FxOut o = fx_out(p, S);
     OutT* dst = (OutT*)p.dst;
@@ -572,7 +587,7 @@ __global__ void __launch_bounds__(kFxThreads, 2) k_fx_strided_c(FxLaunch p, unsi
         const int e = t + u * kFxThreads;
         const uint32_t k = kbase + ((uint32_t)(e >> LW) << b0) + (uint32_t)(e & (kW - 1));
         const uint32_t gi = ((x - (uint32_t)p.dst_row0) << n) + k;
-        if (in_bounds(st, gi, p.dst_elems)) dst[gi] = out_of<OutT>::cvt(s.get(fx_idx<LW>(e)), __popc(x & k) & 3, o);
+        if (in_bounds(st, gi, p.dst_elems)) dst[gi] = out_of<OutT>::cvt(s.get(FxLay<LW>::idx(e)), __popc(x & k) & 3, o);
     }
 }
 
@@ -661,7 +676,7 @@ template <typename InT>
 cudaError_t run_fx_tile_c(const FxLaunch& p, unsigned int* st, cudaStream_t s)
 {
     auto kern = k_fx_tile_c<InT, 2, 9>;
-    const size_t bytes = smem_elems(4, 9) * sizeof(fx2);
+    const size_t bytes = (size_t)4 * FxLayGather::kRs * sizeof(fx2); // two planes of 4 rows
     cudaError_t e = fx_smem(kern, bytes);
     if (e != cudaSuccess) return e;
     const uint64_t blocks = (p.x_count >> 2) << (p.n - 9);

@@ -293,7 +293,7 @@ static ptdr_status decompose_band(const void* bands, ptdr_dtype b_type, int n, i
         p.scale = std::ldexp(1.0, -n);
         const bool single = m.f <= single_log;
         p.log_l = single ? m.f : tile_log;
-        p.threads = ((size_t)1 << p.log_l) * S >= 32 * 1024 ? 512 : 256;
+        p.threads = ((size_t)1 << p.log_l) * S >= 32 * 1024 && calc != Calc::F64 ? 512 : 256;
         // A mask the band cannot reach has no pairs: its row is written as zeros.
         if (m.npairs > 0) e = launch_band_first(p, st, ms);
         if (e == cudaSuccess && m.npairs > 0 && !single) {
@@ -315,7 +315,7 @@ static ptdr_status decompose_band(const void* bands, ptdr_dtype b_type, int n, i
                 sl.src_elems = p.ws_elems;
                 sl.dst_elems = p.ws_elems;
                 sl.scale = 1.0;
-                sl.threads = 512;
+                sl.threads = calc == Calc::F64 ? 256 : 512;
                 sl.real = real;
                 e = launch_strided(sl, st, ms);
             }
